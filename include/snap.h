@@ -1,0 +1,227 @@
+/*
+ * snap.h -- C ABI of libsnap: GPU device-memory snapshot and restore.
+ *
+ * The library implements the data path of transparent GPU checkpointing as
+ * CRIUgpu (arXiv 2502.16631) frames it: a process's device allocations are
+ * copied into a host-memory checkpoint image and later put back byte for byte
+ * (Sec. 3.1.1, the checkpoint and restore actions; Sec. 6, deterministic
+ * restore).  On top of that it adds what Sec. 7 names as optimisations that
+ * could be incorporated: per-chunk CRC-32C hashes and incremental
+ * (dirty-chunk) checkpoints, a batched persistent launch, and a serving loop.
+ *
+ * Conventions for every call:
+ *  - The return value is a status (snap_status); SNAP_OK is 0, errors are
+ *    negative.  snap_strerror() names them.
+ *  - Pointers marked "device" are CUDA device addresses on the set's device;
+ *    "host" pointers are CPU addresses.  No call takes ownership of caller
+ *    memory; the library owns what it allocates (hash tables, descriptors,
+ *    graphs, the pinned ring) and frees it in the matching destroy call.
+ *  - Calls are synchronous: when a call returns SNAP_OK the image (checkpoint)
+ *    or the device buffers (restore) are complete.  The serving API is the
+ *    asynchronous form.
+ *  - One call at a time per set: a call that finds another in progress on the
+ *    same set returns SNAP_EBUSY.  Different sets may be used concurrently.
+ *  - Failure atomicity (the plugin exit callback rolls back on error,
+ *    Sec. 3.1): on any error the set's committed hash table, generation and
+ *    base are unchanged, and no image other than the call's own output
+ *    buffer is modified.
+ */
+#ifndef SNAP_H
+#define SNAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef enum {
+    SNAP_OK = 0,
+    SNAP_EINVAL = -1,     /* bad argument: null pointer, misaligned pointer,
+                             capacity too small, bad option value          */
+    SNAP_ENOMEM = -2,     /* a device, pinned-host or host allocation failed */
+    SNAP_ECUDA = -3,      /* a CUDA runtime call failed, or a kernel reported
+                             an internal error (a bounded wait expired)    */
+    SNAP_ETIMEDOUT = -4,  /* quiesce or completion did not finish before the
+                             deadline (Sec. 3.1.1: the lock action uses a
+                             10 s timeout, then rolls back)               */
+    SNAP_ENOBASE = -5,    /* incremental checkpoint without a committed base */
+    SNAP_EFORMAT = -6,    /* image header/record malformed or truncated     */
+    SNAP_EMISMATCH = -7,  /* image does not fit the set: allocation count or
+                             sizes differ, or patch/base generations differ
+                             (restore needs a compatible target, Sec. 4.4)  */
+    SNAP_EBUSY = -8,      /* another call is in progress on this set        */
+    SNAP_EBUDGET = -9     /* request can never fit the server's budgets     */
+} snap_status;
+
+typedef enum { SNAP_FULL = 0, SNAP_INCREMENTAL = 1 } snap_mode;
+
+/* Serving request kinds. */
+typedef enum { SNAP_REQ_FULL = 0, SNAP_REQ_INCREMENTAL = 1, SNAP_REQ_RESTORE = 2 } snap_req_kind;
+
+typedef struct snap_set_s *snap_set;
+typedef struct snap_server_s *snap_server;
+
+/* Options; a zero field takes the default shown. */
+typedef struct {
+    uint64_t chunk_bytes;  /* hash chunk C: multiple of 4096 in [4 KiB, 16 MiB]; default 65536 */
+    uint32_t timeout_ms;   /* quiesce/completion deadline; default 10000 (Sec. 3.1.1) */
+    int32_t device;        /* CUDA device ordinal; default: the current device */
+    void *stream;          /* caller's cudaStream_t whose queued work must finish
+                              before a snapshot starts (the "lock"); NULL = the
+                              legacy default stream */
+    uint32_t ctas_per_sm;  /* persistent CTAs per SM; 0 = tuned default */
+    uint32_t stages;       /* staging buffers per warp; 0 = tuned default */
+    uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB */
+} snap_opts;
+
+/* Per-call statistics (times in milliseconds; quiesce_ms and total_ms are
+ * host wall time, the others come from CUDA events on the library stream). */
+typedef struct {
+    uint64_t state_bytes;    /* device bytes covered by the call          */
+    uint64_t image_bytes;    /* bytes of image written or read            */
+    uint64_t total_chunks;
+    uint64_t dirty_chunks;   /* incremental: chunks copied                */
+    uint64_t mismatches;     /* verify: chunks whose hash differs         */
+    uint64_t generation;     /* generation of the image written/restored  */
+    double quiesce_ms;
+    double hash_ms;          /* hash pass (incremental / verify)          */
+    double diff_ms;          /* dirty diff + compaction + patch layout    */
+    double copy_ms;          /* gather (checkpoint) or scatter (restore)  */
+    double total_ms;         /* call entry to return                      */
+} snap_stats;
+
+/* ------------------------------------------------------------------ sets */
+/* Create an empty set of device allocations on o->device.  o may be NULL.
+ * *out receives the handle (owned by the library; free with
+ * snap_set_destroy).  Errors: EINVAL (bad option), ENOMEM, ECUDA. */
+int snap_set_create(snap_set *out, const snap_opts *o);
+
+/* Release everything the set owns.  Caller memory is untouched. */
+int snap_set_destroy(snap_set s);
+
+/* Register a device allocation [dptr, dptr+bytes) (Sec. 3.1.1: the device
+ * memory a checkpoint captures).  dptr must be a device pointer of the set's
+ * device, 16-byte aligned (cudaMalloc and torch allocations are); bytes may
+ * be anything, including 0.  Allocations keep registration order in the
+ * image.  The caller keeps ownership and must keep the memory alive while
+ * registered.  Registering after a checkpoint drops the committed base (the
+ * next incremental returns ENOBASE).  Returns the allocation index (>= 0) or
+ * an error (EINVAL, EBUSY). */
+int snap_register(snap_set s, void *dptr, uint64_t bytes);
+
+/* Bytes a host image needs: exact for SNAP_FULL; an upper bound for
+ * SNAP_INCREMENTAL (the patch size depends on how many chunks are dirty). */
+int snap_image_bytes(snap_set s, int mode, uint64_t *out);
+
+/* Pinned, device-mapped host memory for images (cudaHostAlloc, mapped and
+ * portable).  Images in such memory are written/read by the kernels directly
+ * over the host link; any other (pageable) image goes through the set's
+ * pinned ring.  Free with snap_host_free.  Errors: EINVAL, ENOMEM. */
+int snap_host_alloc(uint64_t bytes, void **out);
+int snap_host_free(void *p);
+
+/* --------------------------------------------------------- checkpoint path */
+/* Checkpoint the set into host_image[0..cap) (16-byte aligned).
+ *  SNAP_FULL: writes the full image: 64-byte header, then per allocation a
+ *    32-byte record {bytes, n_chunks, data_offset, 0}, the CRC-32C of every
+ *    chunk, padding to 4 KiB, the bytes, padding to 4 KiB (layout in
+ *    snap_format.h).  Sec. 3.1.1 "checkpoint".
+ *  SNAP_INCREMENTAL: hashes every chunk, diffs against the committed hash
+ *    table, and writes a patch holding all new hashes, the ascending list of
+ *    dirty chunks and only their bytes.  Needs a committed base (ENOBASE).
+ * Steps: quiesce the caller's stream with the deadline (the "lock",
+ * Sec. 3.1.1), run the graph-captured persistent kernels, wait with the
+ * deadline, then commit the new hash table and generation.  *used receives
+ * the image size.  Errors: EINVAL (cap too small: nothing committed),
+ * ENOBASE, ETIMEDOUT, EBUSY, ENOMEM, ECUDA. */
+int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used);
+
+/* Restore a full image into the set's registered buffers (Sec. 3.1.1
+ * "restore"; Sec. 6).  The image must describe the same allocation count and
+ * sizes (EMISMATCH otherwise) and be well formed (EFORMAT; a patch must first
+ * be merged with snap_apply_patch).  The image's hashes become the committed
+ * base.  Errors: EINVAL, EFORMAT, EMISMATCH, ETIMEDOUT, EBUSY, ECUDA. */
+int snap_restore(const void *host_image, uint64_t bytes, snap_set s);
+
+/* Re-hash the device state and compare every chunk with the hashes stored in
+ * host_image (a full image or a patch).  *n_mismatch = number of differing
+ * chunks.  Sec. 6 (a restore must reproduce the snapshotted state). */
+int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_mismatch);
+
+/* Merge a patch into its base full image in place (host only): dirty chunks
+ * are copied into their slots, all hashes replaced, the generation advanced.
+ * base.generation must equal patch.parent_generation (EMISMATCH); both are
+ * validated completely before the base is modified (EFORMAT leaves it
+ * intact). */
+int snap_apply_patch(void *base_image, uint64_t base_bytes, const void *patch, uint64_t patch_bytes);
+
+/* Copy the committed hash table (all chunks, registration order) to host
+ * out[0..n) and its generation; EINVAL if n is smaller than the chunk count,
+ * ENOBASE if nothing is committed. */
+int snap_committed_hashes(snap_set s, uint32_t *out, uint64_t n, uint64_t *generation);
+
+/* Statistics of the set's last successful call. */
+int snap_last_stats(snap_set s, snap_stats *out);
+
+/* Static message for a status code. */
+const char *snap_strerror(int status);
+
+/* ------------------------------------------------------------- plain form */
+/* The comparison baseline, not a fallback: one cudaMemcpyAsync per
+ * allocation between the device buffers and the data regions of a full
+ * image (no hashes, no header), full copy every time. */
+int snap_plain_checkpoint(snap_set s, void *host_image, uint64_t cap);
+int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s);
+
+/* ------------------------------------------------------------- hashing */
+/* Standalone chunk hasher: hashes[i] = CRC-32C of bytes [i*C, min((i+1)*C,
+ * bytes)) of the device buffer dptr (16-byte aligned); hashes is a device
+ * array of ceil(bytes/C) entries; C = chunk_bytes as for snap_opts.  Runs on
+ * `stream` (cudaStream_t, NULL = legacy default) and waits for it.  Uses
+ * library-owned device scratch (allocated on the first call per device). */
+int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_bytes,
+                     uint32_t *hashes, void *stream);
+
+/* ----------------------------------------------------------- autotuning */
+typedef struct {
+    uint32_t warps;        /* warps per CTA of the persistent kernel */
+    uint32_t stages;       /* staging buffers per warp               */
+    uint32_t piece_bytes;  /* bytes each lane stages per step        */
+    uint32_t ctas_per_sm;
+    double gbs;            /* measured throughput of the winner      */
+} snap_tuning;
+
+/* Time the set's hash pass (mode SNAP_INCREMENTAL) or full gather (SNAP_FULL)
+ * over a grid of launch shapes, adopt the fastest for this set, and record it
+ * in the tuning cache keyed by (GPU name, operation, chunk size, state size
+ * class); the cache file is $SNAP_TUNE_CACHE if set.  The device state is
+ * read, never modified.  host_image (SNAP_FULL only) is a scratch image of
+ * snap_image_bytes(FULL) bytes in snap_host_alloc memory. */
+int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap, snap_tuning *out);
+
+/* ------------------------------------------------------------- serving */
+/* A request loop over many tenant sets: requests are admitted as pinned-host
+ * and HBM budget frees up, and the chunk tiles of all admitted requests are
+ * batched into shared persistent launches (continuous batching), so requests
+ * that arrive while others run overlap on the device. */
+int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_budget,
+                       const snap_opts *o);
+int snap_server_destroy(snap_server sv);
+/* Queue a request on tenant set `tenant` (created on the server's device).
+ * kind: SNAP_REQ_FULL / SNAP_REQ_INCREMENTAL write `image` (cap bytes);
+ * SNAP_REQ_RESTORE reads it.  *ticket identifies it.  EBUDGET if it can never
+ * be admitted under the budgets. */
+int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, uint64_t cap,
+                       uint64_t *ticket);
+/* Wait up to timeout_ms for a ticket; *status gets the request's own status,
+ * st (may be NULL) its statistics with total_ms = arrival-to-completion
+ * latency.  Returns ETIMEDOUT if it is still running. */
+int snap_server_wait(snap_server sv, uint64_t ticket, uint32_t timeout_ms, int *status,
+                     snap_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SNAP_H */

@@ -1,0 +1,517 @@
+// Device kernels of libsnap (sm_103a): the persistent tile kernel.
+//
+// The hot path of a GPU checkpoint (CRIUgpu, Sec. 3.1.1: device memory is
+// copied into host memory; restore copies it back) plus the chunk hashing
+// that incremental checkpointing adds (Sec. 7).
+//
+// One persistent kernel (snap_tiles) serves every operation: each warp pulls
+// (allocation, chunk) tiles from a device-side cursor across a list of jobs
+// and runs the job's operation on its chunk:
+//   OP_GATHER        TMA bulk copy HBM -> shared memory in 32*P-byte stages,
+//                    CRC-32C from shared memory, 128-bit stores to the mapped
+//                    host image (the device -> host link is the bound);
+//   OP_HASH/VERIFY   128-bit cp.async staging of lane-contiguous segments in
+//                    a padded, bank-conflict-free layout, CRC-32C per lane,
+//                    warp-shuffle combine through GF(2) shift constants (HBM
+//                    read is the bound);
+//   OP_GATHER_DIRTY  the gather path without hashing, into patch slots;
+//   OP_SCATTER       128-bit loads from the mapped host image, stores to HBM
+//                    (host -> device link is the bound).
+// CRC-32C lookups use slicing-by-4 tables replicated once per lane so that
+// every lane reads its own shared-memory bank (lookups never conflict).
+//
+// Every wait is bounded: an mbarrier wait gives up after kWaitNs, records
+// ERR_WAIT_TIMEOUT, drains the warp's outstanding copies (again bounded) and
+// the warp leaves.  No wait depends on the host or on another kernel.
+#include "snap_internal.h"
+#include "crc32c_gf2.h"
+
+namespace snapk {
+
+__device__ const SliceTables g_slice = make_slice_tables();
+__constant__ Pow8Table c_pow8 = make_pow8_table();
+
+constexpr uint32_t kTableBytes = 4 * 256 * 32 * 4;     // 4 tables x 256 x 32 lanes
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+
+size_t tile_smem_bytes(const TileShape &sh)
+{
+    return kTableBytes + (size_t)sh.warps * sh.stages * 32 * (sh.piece + 16) +
+           (size_t)sh.warps * sh.stages * 8 + (kMaxJobs + 1) * 8;
+}
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of phase `parity` of the mbarrier at a.
+__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity)
+{
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try(a, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(128);
+    }
+}
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint32_t mbar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ------------------------------------------------------------- CRC pieces
+// tl points at this lane's column of the replicated tables: entry (t, v) of
+// slicing table t is tl[(t * 256 + v) * 32], always in bank == lane.
+__device__ __forceinline__ uint32_t crc_word(uint32_t crc, uint32_t w, const uint32_t *tl)
+{
+    const uint32_t x = crc ^ w;
+    return tl[(768u + (x & 0xFFu)) << 5] ^ tl[(512u + ((x >> 8) & 0xFFu)) << 5] ^
+           tl[(256u + ((x >> 16) & 0xFFu)) << 5] ^ tl[(x >> 24) << 5];
+}
+__device__ __forceinline__ uint32_t crc_byte(uint32_t crc, uint32_t b, const uint32_t *tl)
+{
+    return tl[((crc ^ b) & 0xFFu) << 5] ^ (crc >> 8);
+}
+__device__ __forceinline__ uint32_t crc_block(uint32_t crc, const uint4 v, const uint32_t *tl)
+{
+    crc = crc_word(crc, v.x, tl);
+    crc = crc_word(crc, v.y, tl);
+    crc = crc_word(crc, v.z, tl);
+    return crc_word(crc, v.w, tl);
+}
+__device__ __forceinline__ uint32_t warp_xor(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v ^= __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t up_page(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
+
+// Warp-cooperative zero fill of host memory [p, p+n).
+__device__ void warp_zero(uint8_t *p, uint64_t n, int lane)
+{
+    uint64_t head = (16u - ((uintptr_t)p & 15u)) & 15u;
+    if (head > n) head = n;
+    if ((uint64_t)lane < head) p[lane] = 0;
+    p += head;
+    n -= head;
+    const uint64_t n16 = n >> 4;
+    for (uint64_t q = lane; q < n16; q += 32) reinterpret_cast<uint4 *>(p)[q] = make_uint4(0, 0, 0, 0);
+    const uint64_t rem = n & 15u;
+    if ((uint64_t)lane < rem) p[(n16 << 4) + lane] = 0;
+}
+
+// ------------------------------------------------------------ warp state
+struct WarpCtx {
+    uint8_t *stage;        // this warp's stage buffers
+    uint32_t mbar;         // shared address of its first mbarrier
+    uint32_t issued;       // stages issued so far (per warp, across chunks)
+    uint32_t consumed;     // stages consumed so far
+    int stages, piece, lane;
+    const uint32_t *tl;    // lane column of the CRC tables
+    uint32_t stage_bytes;  // 32 * (piece + 16)
+};
+
+__device__ __forceinline__ uint32_t buf_of(const WarpCtx &w, uint32_t g) { return g % (uint32_t)w.stages; }
+__device__ __forceinline__ uint32_t par_of(const WarpCtx &w, uint32_t g) { return (g / (uint32_t)w.stages) & 1u; }
+
+// Wait (bounded) for every issued, unconsumed stage: used when giving up.
+__device__ void drain(WarpCtx &w)
+{
+    for (uint32_t g = w.consumed; g < w.issued; ++g) (void)mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g));
+    w.consumed = w.issued;
+}
+
+// ------------------------------------------- segmented hash (HBM-bound path)
+// Lane l owns bytes [l*s, min((l+1)*s, L)) of the chunk; stage k holds the
+// next P bytes of every lane's segment in slot l (stride P + 16, so the
+// 16-byte reads of 8 consecutive lanes hit 8 different bank groups).  Each
+// cp.async instruction of the warp moves four whole 128-byte lines.
+__device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t s, uint32_t k)
+{
+    const uint32_t g = w.issued++;
+    const uint32_t P = (uint32_t)w.piece;
+    uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+    const uint32_t sbs = smem_addr(sb);
+    const uint32_t bpp = P >> 4;  // 16-byte blocks per piece
+    for (uint32_t m = 0; m < bpp; ++m) {
+        const uint32_t q = m * 32u + (uint32_t)w.lane;
+        const uint32_t j = q / bpp, b = q - j * bpp;
+        const uint32_t plo = j * s + k * P;
+        uint32_t phi = plo + P;
+        const uint32_t seg_hi = j * s + s;
+        if (phi > seg_hi) phi = seg_hi;
+        if (phi > L) phi = L;
+        if (plo + 16u * b + 16u <= phi) cp_async16(sbs + j * (P + 16u) + 16u * b, src + plo + 16u * b);
+    }
+    cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+}
+
+// The chunk's CRC-32C lands in `out` in every lane; false if a wait gave up.
+__device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t C, const CombineConsts &cc,
+                               uint32_t &out)
+{
+    const int lane = w.lane;
+    const uint32_t P = (uint32_t)w.piece;
+    const uint32_t s = (L == C) ? (C >> 5) : ((((L + 31u) >> 5) + 15u) & ~15u);
+    const uint32_t nst = (s + P - 1) / P;
+    uint32_t lo = (uint32_t)lane * s;
+    if (lo > L) lo = L;
+    uint32_t hi = lo + s;
+    if (hi > L) hi = L;
+    uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
+
+    const uint32_t pre = nst < (uint32_t)w.stages ? nst : (uint32_t)w.stages;
+    for (uint32_t k = 0; k < pre; ++k) seg_issue(w, src, L, s, k);
+    for (uint32_t k = 0; k < nst; ++k) {
+        const uint32_t g = w.consumed;
+        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
+        w.consumed++;
+        const uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+        const uint32_t plo = lo + k * P;
+        if (plo < hi) {
+            const uint32_t phi = plo + P < hi ? plo + P : hi;
+            const uint4 *sp = reinterpret_cast<const uint4 *>(sb + lane * (P + 16u));
+            const uint32_t nfull = (phi - plo) >> 4;
+            if (nfull == (P >> 4)) {
+#pragma unroll 4
+                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.tl);
+            } else {
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.tl);
+            }
+            const uint32_t rem = (phi - plo) & 15u;
+            if (rem) {
+                const uint8_t *tp = src + plo + (nfull << 4);
+                for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.tl);
+            }
+        }
+        __syncwarp();
+        if (k + (uint32_t)w.stages < nst) seg_issue(w, src, L, s, k + (uint32_t)w.stages);
+    }
+    uint32_t v = 0;
+    if (lo < L) {
+        const uint32_t K = (L == C) ? cc.kseg[lane] : gf2_x8n(L - hi, c_pow8);
+        v = gf2_mulmod(crc, K);
+    }
+    out = warp_xor(v) ^ 0xFFFFFFFFu;
+    return true;
+}
+
+// ------------------------------------ interleaved gather (link-bound path)
+// Stage k is the contiguous range [k*32P, (k+1)*32P) of the chunk, moved by
+// one TMA bulk copy; lane l hashes its piece [k*32P + l*P, +P), so its pieces
+// are 31*P bytes apart (the gap is shifted in with the constant kgap), and
+// the warp stores the stage to the host as contiguous 512-byte rows.
+__device__ __forceinline__ void int_issue(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t k)
+{
+    const uint32_t g = w.issued++;
+    const uint32_t SB = 32u * (uint32_t)w.piece;
+    const uint32_t mb = w.mbar + 8 * buf_of(w, g);
+    if (w.lane == 0) {
+        const uint32_t lo = k * SB;
+        const uint32_t slen = (L - lo) < SB ? (L - lo) : SB;
+        const uint32_t n16 = slen & ~15u;
+        mbar_arrive_tx(mb, n16);
+        if (n16) tma_load_1d(smem_addr(w.stage + buf_of(w, g) * w.stage_bytes), src + lo, n16, mb);
+    } else {
+        mbar_arrive(mb);
+    }
+}
+
+__device__ bool gather_chunk_int(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t C, bool do_hash,
+                                 uint8_t *dst, const CombineConsts &cc, uint32_t &out)
+{
+    const int lane = w.lane;
+    const uint32_t P = (uint32_t)w.piece;
+    const uint32_t SB = 32u * P;
+    const uint32_t nst = (L + SB - 1) / SB;
+    uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
+    uint32_t e = 0;  // end of this lane's last hashed piece
+
+    const uint32_t pre = nst < (uint32_t)w.stages ? nst : (uint32_t)w.stages;
+    for (uint32_t k = 0; k < pre; ++k) int_issue(w, src, L, k);
+    for (uint32_t k = 0; k < nst; ++k) {
+        const uint32_t g = w.consumed;
+        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
+        w.consumed++;
+        const uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+        const uint32_t slo = k * SB;
+        const uint32_t slen = (L - slo) < SB ? (L - slo) : SB;
+        const uint32_t n16 = slen & ~15u;
+        if (do_hash) {
+            const uint32_t plo = slo + (uint32_t)lane * P;
+            if (plo < L) {
+                const uint32_t phi = plo + P < L ? plo + P : L;
+                const uint32_t gap = plo - e;
+                if (crc != 0u && gap != 0u) crc = gf2_mulmod(crc, gap == 31u * P ? cc.kgap : gf2_x8n(gap, c_pow8));
+                const uint4 *sp = reinterpret_cast<const uint4 *>(sb + (uint32_t)lane * P);
+                const uint32_t nfull = (phi - plo) >> 4;
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.tl);
+                const uint32_t rem = (phi - plo) & 15u;
+                if (rem) {
+                    const uint8_t *tp = src + plo + (nfull << 4);
+                    for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.tl);
+                }
+                e = phi;
+            }
+        }
+        // stage -> host as contiguous 16-byte columns of the warp
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(sb);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + slo);
+        const uint32_t nb = n16 >> 4;
+        for (uint32_t q = (uint32_t)lane; q < nb; q += 32u) d4[q] = s4[q];
+        if (slen != n16 && lane == 0)
+            for (uint32_t r = n16; r < slen; ++r) dst[slo + r] = __ldg(src + slo + r);
+        __syncwarp();
+        if (k + (uint32_t)w.stages < nst) {
+            fence_proxy_async();
+            int_issue(w, src, L, k + (uint32_t)w.stages);
+        }
+    }
+    if (do_hash) {
+        uint32_t v = 0;
+        if (e != 0u) {
+            const uint32_t K = (L == C && C % SB == 0u) ? cc.kint[lane] : gf2_x8n(L - e, c_pow8);
+            v = gf2_mulmod(crc, K);
+        }
+        out = warp_xor(v) ^ 0xFFFFFFFFu;
+    }
+    return true;
+}
+
+// ------------------------------------------------- scatter (host -> device)
+__device__ void scatter_chunk(const uint8_t *src, uint8_t *dst, uint32_t L, int lane)
+{
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    const uint32_t nb = L >> 4;
+    constexpr uint32_t U = 8;
+    uint32_t q = (uint32_t)lane;
+    for (; q + 32u * (U - 1) < nb; q += 32u * U) {
+        uint4 v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) v[u] = s4[q + 32u * u];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) d4[q + 32u * u] = v[u];
+    }
+    for (; q < nb; q += 32u) d4[q] = s4[q];
+    const uint32_t rem = L & 15u;
+    if ((uint32_t)lane < rem) dst[(nb << 4) + lane] = src[(nb << 4) + lane];
+}
+
+// -------------------------------------------------------------- main kernel
+// Largest k with a[k].chunk0 <= chunk (ties: the largest index, so that
+// zero-byte allocations, which own no chunk, are never chosen).
+__device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, uint64_t chunk)
+{
+    uint64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid].chunk0 <= chunk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kMaxWarps * 32, 1)
+snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor, const CombineConsts cc,
+           int stages, int piece, Result *kres)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint32_t *tables = reinterpret_cast<uint32_t *>(smem);
+    const int warps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stage_bytes = 32u * (uint32_t)(piece + 16);
+    uint8_t *stage_all = smem + kTableBytes;
+    uint64_t *mbars = reinterpret_cast<uint64_t *>(stage_all + (size_t)warps * stages * stage_bytes);
+    unsigned long long *prefix = reinterpret_cast<unsigned long long *>(mbars + warps * stages);
+
+    bool need_tables = false;
+    for (int j = 0; j < n_jobs; ++j)
+        need_tables |= (jobs[j].op == OP_HASH || jobs[j].op == OP_GATHER || jobs[j].op == OP_VERIFY);
+    if (need_tables)
+        for (int i = threadIdx.x; i < 32768; i += blockDim.x) {
+            const int tv = i >> 5;
+            tables[i] = g_slice.t[tv >> 8][tv & 255];
+        }
+    if (lane == 0)
+        for (int s = 0; s < stages; ++s) mbar_init(smem_addr(&mbars[warp * stages + s]), 32);
+    if (threadIdx.x == 0) {
+        prefix[0] = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            const Job &jb = jobs[j];
+            const unsigned long long n = jb.n_tiles_dev ? *jb.n_tiles_dev : jb.n_tiles;
+            prefix[j + 1] = prefix[j] + n;
+        }
+    }
+    fence_mbar_init();
+    __syncthreads();
+    const unsigned long long total = prefix[n_jobs];
+
+    WarpCtx w;
+    w.stage = stage_all + (size_t)warp * stages * stage_bytes;
+    w.mbar = smem_addr(&mbars[warp * stages]);
+    w.issued = w.consumed = 0;
+    w.stages = stages;
+    w.piece = piece;
+    w.lane = lane;
+    w.tl = tables + lane;
+    w.stage_bytes = stage_bytes;
+
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(cursor, 1ull);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if (t >= total) break;
+        if (*reinterpret_cast<volatile unsigned long long *>(&kres->err)) break;
+        int j = 0;
+        while (j + 1 < n_jobs && prefix[j + 1] <= t) ++j;
+        const Job &jb = jobs[j];
+        const unsigned long long tt = t - prefix[j];
+        const uint64_t chunk = jb.tile_list ? (uint64_t)jb.tile_list[tt] : jb.tile_begin + tt;
+        const uint64_t k = find_alloc(jb.allocs, jb.n_allocs, chunk);
+        const AllocDesc ad = jb.allocs[k];
+        const uint64_t C = jb.chunk_bytes;
+        const uint64_t i = chunk - ad.chunk0;
+        const uint64_t nk = (ad.bytes + C - 1) / C;
+        if (chunk < ad.chunk0 || i >= nk) {
+            if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+            break;
+        }
+        const uint64_t off = i * C;
+        const uint32_t L = (uint32_t)((ad.bytes - off) < C ? (ad.bytes - off) : C);
+        const uint8_t *dsrc = reinterpret_cast<const uint8_t *>(ad.ptr) + off;
+        uint8_t *host_data = jb.layout == LAYOUT_IMAGE ? jb.host + ad.data_off + off
+                                                       : jb.host + (ad.state_off + off - jb.window_off);
+        bool ok = true;
+        uint32_t h = 0;
+        switch (jb.op) {
+        case OP_HASH:
+        case OP_VERIFY:
+            ok = hash_chunk_seg(w, dsrc, L, (uint32_t)C, cc, h);
+            if (ok && lane == 0) {
+                if (jb.hash_out) jb.hash_out[chunk] = h;
+                if (jb.op == OP_VERIFY && jb.hash_cmp[chunk] != h) {
+                    atomicAdd(&jb.res->mismatches, 1ull);
+                    atomicMin(&jb.res->first_bad, (unsigned long long)chunk);
+                }
+            }
+            break;
+        case OP_GATHER:
+            ok = gather_chunk_int(w, dsrc, L, (uint32_t)C, true, host_data, cc, h);
+            if (ok) {
+                if (lane == 0) {
+                    if (jb.hash_out) jb.hash_out[chunk] = h;
+                    if (jb.layout == LAYOUT_IMAGE) *reinterpret_cast<uint32_t *>(jb.host + ad.rec_off + 32 + 4 * i) = h;
+                }
+                if (jb.layout == LAYOUT_IMAGE && i + 1 == nk) {
+                    const uint64_t end = ad.data_off + ad.bytes;
+                    warp_zero(jb.host + end, up_page(end) - end, lane);
+                }
+            }
+            break;
+        case OP_GATHER_DIRTY: {
+            if (*reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) break;
+            uint8_t *dst = jb.host + jb.patch_data[k] + (tt - jb.dstart[k]) * C;
+            ok = gather_chunk_int(w, dsrc, L, (uint32_t)C, false, dst, cc, h);
+            if (ok && (L & 4095u)) warp_zero(dst + L, up_page(L) - L, lane);
+            break;
+        }
+        case OP_SCATTER:
+            scatter_chunk(host_data, reinterpret_cast<uint8_t *>(ad.ptr) + off, L, lane);
+            break;
+        default:
+            break;
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_WAIT_TIMEOUT);
+            drain(w);
+            break;
+        }
+    }
+}
+
+cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor, const CombineConsts &cc,
+                         const TileShape &sh, Result *kres, cudaStream_t st)
+{
+    const size_t smem = tile_smem_bytes(sh);
+    if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxWarps || n_jobs < 1 || n_jobs > kMaxJobs)
+        return cudaErrorInvalidValue;
+    snap_tiles<<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece, kres);
+    return cudaGetLastError();
+}
+
+// Opt the kernel into the full shared-memory carve-out; call once per
+// device, outside any stream capture.
+cudaError_t init_tile_kernel()
+{
+    return cudaFuncSetAttribute(snap_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+}
+
+CombineConsts make_combine_consts(uint64_t C, int piece)
+{
+    static constexpr Pow8Table pw = make_pow8_table();
+    CombineConsts cc{};
+    const uint64_t s = C / 32;
+    const uint64_t P = (uint64_t)piece;
+    for (int l = 0; l < 32; ++l) {
+        cc.kseg[l] = gf2_x8n(C - (uint64_t)(l + 1) * s, pw);
+        cc.kint[l] = gf2_x8n((uint64_t)(31 - l) * P, pw);
+    }
+    cc.kgap = gf2_x8n(31 * P, pw);
+    return cc;
+}
+
+}  // namespace snapk

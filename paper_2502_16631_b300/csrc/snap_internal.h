@@ -1,0 +1,115 @@
+// Internal structures shared by the kernels (kernels.cu, meta_kernels.cu)
+// and the host runtime (runtime.cu).  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+#include <cuda_runtime.h>
+
+namespace snapk {
+
+// One registered allocation, as the kernels see it (device array).
+struct AllocDesc {
+    uint64_t ptr;        // device address (16-byte aligned)
+    uint64_t bytes;      // size in bytes
+    uint64_t chunk0;     // global index of its first chunk
+    uint64_t rec_off;    // full image: offset of its 32-byte record
+    uint64_t data_off;   // full image: offset of its data (4 KiB aligned)
+    uint64_t state_off;  // offset in the concatenation of all allocations
+};
+
+// What a job does with each of its chunk tiles.
+enum JobOp : uint32_t {
+    OP_HASH = 0,          // CRC every chunk -> hash_out
+    OP_GATHER = 1,        // CRC + copy device -> host, hashes -> hash_out (and image)
+    OP_VERIFY = 2,        // CRC, compare with hash_cmp
+    OP_GATHER_DIRTY = 3,  // copy dirty chunks device -> patch data slots
+    OP_SCATTER = 4,       // copy host -> device
+};
+
+// Where a job's host bytes live.
+enum JobLayout : uint32_t {
+    LAYOUT_IMAGE = 0,   // full-image layout (data at AllocDesc.data_off)
+    LAYOUT_PACKED = 1,  // packed window: host = base + state_off + i*C - window_off
+};
+
+// Device-side outcome of a launch sequence.
+struct Result {
+    unsigned long long err;          // ResultErr bits set by a kernel that gave up
+    unsigned long long mismatches;   // verify
+    unsigned long long first_bad;    // verify: smallest mismatching chunk (or ~0)
+    unsigned long long n_dirty;      // incremental: dirty chunk count
+    unsigned long long patch_bytes;  // incremental: patch size
+    unsigned long long cap_exceeded; // incremental: patch larger than the image capacity
+    unsigned long long pad[2];
+};
+
+enum ResultErr : unsigned long long {
+    ERR_WAIT_TIMEOUT = 1ull,   // an mbarrier wait passed its deadline
+    ERR_BAD_TILE = 2ull,       // a tile resolved outside its allocation table
+};
+
+// One job: a set of chunk tiles with one operation.
+struct Job {
+    const AllocDesc *allocs;
+    uint64_t n_allocs;
+    uint64_t chunk_bytes;
+    uint64_t tile_begin;           // identity tiles: first global chunk
+    uint64_t n_tiles;              // identity tiles: count
+    const uint32_t *tile_list;     // list tiles (ascending global chunks), or null
+    const unsigned long long *n_tiles_dev;  // list tiles: count on the device
+    uint8_t *host;                 // device-visible address of the host image / window
+    uint64_t window_off;           // LAYOUT_PACKED
+    uint32_t op;                   // JobOp
+    uint32_t layout;               // JobLayout
+    uint32_t *hash_out;            // device hash table (global chunk index), or null
+    const uint32_t *hash_cmp;      // OP_VERIFY: expected hashes (global chunk index)
+    const uint64_t *patch_data;    // OP_GATHER_DIRTY: per-allocation data offset in the patch
+    const uint64_t *dstart;        // OP_GATHER_DIRTY: per-allocation first dirty rank
+    const unsigned long long *cap_exceeded;  // OP_GATHER_DIRTY: skip if set
+    Result *res;                   // per-job counters (verify)
+};
+
+constexpr int kMaxJobs = 64;
+constexpr int kMaxWarps = 16;
+
+// Launch shape of the persistent tile kernel.
+struct TileShape {
+    int warps;        // warps per CTA
+    int stages;       // staging buffers per warp
+    int piece;        // bytes per lane per stage: 64, 128 or 256
+    int ctas;         // grid size (persistent CTAs)
+};
+
+// Combine constants, computed on the host for a chunk size and piece size.
+struct CombineConsts {
+    uint32_t kseg[32];    // x^(8*(C - (l+1)*C/32)): segmented lane l of a full chunk
+    uint32_t kint[32];    // x^(8*(31-l)*P): interleaved lane l, end of a full chunk
+    uint32_t kgap;        // x^(8*31*P): interleaved gap between a lane's pieces
+    uint32_t pad[3];
+};
+
+size_t tile_smem_bytes(const TileShape &sh);
+constexpr size_t kMaxSmem = 232448;  // 227 KiB opt-in per CTA
+
+// Kernel launchers.  All run on `st`.
+cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor,
+                         const CombineConsts &cc, const TileShape &sh, Result *kres,
+                         cudaStream_t st);
+CombineConsts make_combine_consts(uint64_t chunk_bytes, int piece);
+cudaError_t init_tile_kernel();
+cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
+                             uint8_t *image, cudaStream_t st);
+cudaError_t launch_diff(const uint32_t *cur, const uint32_t *prev, uint64_t n_chunks,
+                        unsigned int *blockcnt, unsigned long long *blockoff, uint32_t *dlist,
+                        Result *res, cudaStream_t st);
+cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
+                                const uint32_t *dlist, uint64_t *patch_rec, uint64_t *patch_data,
+                                uint64_t *dstart, uint64_t cap, Result *res, cudaStream_t st);
+cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
+                              const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
+                              const uint64_t *patch_data, const uint64_t *dstart,
+                              const Result *res, uint8_t *image, cudaStream_t st);
+
+constexpr int kDiffBlock = 1024;
+
+}  // namespace snapk
