@@ -31,6 +31,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define SNAP_API __attribute__((visibility("default")))
+#else
+#define SNAP_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -67,7 +73,7 @@ typedef struct snap_server_s *snap_server;
 typedef struct {
     uint64_t chunk_bytes;  /* hash chunk C: multiple of 4096 in [4 KiB, 16 MiB]; default 65536 */
     uint32_t timeout_ms;   /* quiesce/completion deadline; default 10000 (Sec. 3.1.1) */
-    int32_t device;        /* CUDA device ordinal; default: the current device */
+    int32_t device;        /* CUDA device ordinal; -1 = the current device */
     void *stream;          /* caller's cudaStream_t whose queued work must finish
                               before a snapshot starts (the "lock"); NULL = the
                               legacy default stream */
@@ -96,10 +102,10 @@ typedef struct {
 /* Create an empty set of device allocations on o->device.  o may be NULL.
  * *out receives the handle (owned by the library; free with
  * snap_set_destroy).  Errors: EINVAL (bad option), ENOMEM, ECUDA. */
-int snap_set_create(snap_set *out, const snap_opts *o);
+SNAP_API int snap_set_create(snap_set *out, const snap_opts *o);
 
 /* Release everything the set owns.  Caller memory is untouched. */
-int snap_set_destroy(snap_set s);
+SNAP_API int snap_set_destroy(snap_set s);
 
 /* Register a device allocation [dptr, dptr+bytes) (Sec. 3.1.1: the device
  * memory a checkpoint captures).  dptr must be a device pointer of the set's
@@ -109,18 +115,18 @@ int snap_set_destroy(snap_set s);
  * registered.  Registering after a checkpoint drops the committed base (the
  * next incremental returns ENOBASE).  Returns the allocation index (>= 0) or
  * an error (EINVAL, EBUSY). */
-int snap_register(snap_set s, void *dptr, uint64_t bytes);
+SNAP_API int snap_register(snap_set s, void *dptr, uint64_t bytes);
 
 /* Bytes a host image needs: exact for SNAP_FULL; an upper bound for
  * SNAP_INCREMENTAL (the patch size depends on how many chunks are dirty). */
-int snap_image_bytes(snap_set s, int mode, uint64_t *out);
+SNAP_API int snap_image_bytes(snap_set s, int mode, uint64_t *out);
 
 /* Pinned, device-mapped host memory for images (cudaHostAlloc, mapped and
  * portable).  Images in such memory are written/read by the kernels directly
  * over the host link; any other (pageable) image goes through the set's
  * pinned ring.  Free with snap_host_free.  Errors: EINVAL, ENOMEM. */
-int snap_host_alloc(uint64_t bytes, void **out);
-int snap_host_free(void *p);
+SNAP_API int snap_host_alloc(uint64_t bytes, void **out);
+SNAP_API int snap_host_free(void *p);
 
 /* --------------------------------------------------------- checkpoint path */
 /* Checkpoint the set into host_image[0..cap) (16-byte aligned).
@@ -136,44 +142,44 @@ int snap_host_free(void *p);
  * deadline, then commit the new hash table and generation.  *used receives
  * the image size.  Errors: EINVAL (cap too small: nothing committed),
  * ENOBASE, ETIMEDOUT, EBUSY, ENOMEM, ECUDA. */
-int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used);
+SNAP_API int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used);
 
 /* Restore a full image into the set's registered buffers (Sec. 3.1.1
  * "restore"; Sec. 6).  The image must describe the same allocation count and
  * sizes (EMISMATCH otherwise) and be well formed (EFORMAT; a patch must first
  * be merged with snap_apply_patch).  The image's hashes become the committed
  * base.  Errors: EINVAL, EFORMAT, EMISMATCH, ETIMEDOUT, EBUSY, ECUDA. */
-int snap_restore(const void *host_image, uint64_t bytes, snap_set s);
+SNAP_API int snap_restore(const void *host_image, uint64_t bytes, snap_set s);
 
 /* Re-hash the device state and compare every chunk with the hashes stored in
  * host_image (a full image or a patch).  *n_mismatch = number of differing
  * chunks.  Sec. 6 (a restore must reproduce the snapshotted state). */
-int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_mismatch);
+SNAP_API int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_mismatch);
 
 /* Merge a patch into its base full image in place (host only): dirty chunks
  * are copied into their slots, all hashes replaced, the generation advanced.
  * base.generation must equal patch.parent_generation (EMISMATCH); both are
  * validated completely before the base is modified (EFORMAT leaves it
  * intact). */
-int snap_apply_patch(void *base_image, uint64_t base_bytes, const void *patch, uint64_t patch_bytes);
+SNAP_API int snap_apply_patch(void *base_image, uint64_t base_bytes, const void *patch, uint64_t patch_bytes);
 
 /* Copy the committed hash table (all chunks, registration order) to host
  * out[0..n) and its generation; EINVAL if n is smaller than the chunk count,
  * ENOBASE if nothing is committed. */
-int snap_committed_hashes(snap_set s, uint32_t *out, uint64_t n, uint64_t *generation);
+SNAP_API int snap_committed_hashes(snap_set s, uint32_t *out, uint64_t n, uint64_t *generation);
 
 /* Statistics of the set's last successful call. */
-int snap_last_stats(snap_set s, snap_stats *out);
+SNAP_API int snap_last_stats(snap_set s, snap_stats *out);
 
 /* Static message for a status code. */
-const char *snap_strerror(int status);
+SNAP_API const char *snap_strerror(int status);
 
 /* ------------------------------------------------------------- plain form */
 /* The comparison baseline, not a fallback: one cudaMemcpyAsync per
  * allocation between the device buffers and the data regions of a full
  * image (no hashes, no header), full copy every time. */
-int snap_plain_checkpoint(snap_set s, void *host_image, uint64_t cap);
-int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s);
+SNAP_API int snap_plain_checkpoint(snap_set s, void *host_image, uint64_t cap);
+SNAP_API int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s);
 
 /* ------------------------------------------------------------- hashing */
 /* Standalone chunk hasher: hashes[i] = CRC-32C of bytes [i*C, min((i+1)*C,
@@ -181,7 +187,7 @@ int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s);
  * array of ceil(bytes/C) entries; C = chunk_bytes as for snap_opts.  Runs on
  * `stream` (cudaStream_t, NULL = legacy default) and waits for it.  Uses
  * library-owned device scratch (allocated on the first call per device). */
-int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_bytes,
+SNAP_API int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_bytes,
                      uint32_t *hashes, void *stream);
 
 /* ----------------------------------------------------------- autotuning */
@@ -199,26 +205,26 @@ typedef struct {
  * class); the cache file is $SNAP_TUNE_CACHE if set.  The device state is
  * read, never modified.  host_image (SNAP_FULL only) is a scratch image of
  * snap_image_bytes(FULL) bytes in snap_host_alloc memory. */
-int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap, snap_tuning *out);
+SNAP_API int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap, snap_tuning *out);
 
 /* ------------------------------------------------------------- serving */
 /* A request loop over many tenant sets: requests are admitted as pinned-host
  * and HBM budget frees up, and the chunk tiles of all admitted requests are
  * batched into shared persistent launches (continuous batching), so requests
  * that arrive while others run overlap on the device. */
-int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_budget,
+SNAP_API int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_budget,
                        const snap_opts *o);
-int snap_server_destroy(snap_server sv);
+SNAP_API int snap_server_destroy(snap_server sv);
 /* Queue a request on tenant set `tenant` (created on the server's device).
  * kind: SNAP_REQ_FULL / SNAP_REQ_INCREMENTAL write `image` (cap bytes);
  * SNAP_REQ_RESTORE reads it.  *ticket identifies it.  EBUDGET if it can never
  * be admitted under the budgets. */
-int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, uint64_t cap,
+SNAP_API int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, uint64_t cap,
                        uint64_t *ticket);
 /* Wait up to timeout_ms for a ticket; *status gets the request's own status,
  * st (may be NULL) its statistics with total_ms = arrival-to-completion
  * latency.  Returns ETIMEDOUT if it is still running. */
-int snap_server_wait(snap_server sv, uint64_t ticket, uint32_t timeout_ms, int *status,
+SNAP_API int snap_server_wait(snap_server sv, uint64_t ticket, uint32_t timeout_ms, int *status,
                      snap_stats *st);
 
 #ifdef __cplusplus

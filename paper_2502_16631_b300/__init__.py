@@ -1,0 +1,325 @@
+"""Python binding of libsnap (GPU device-memory snapshot/restore, sm_103a).
+
+Argument marshalling only: every step of the snapshot path runs in the CUDA
+kernels of ``libsnap.so`` behind the C ABI declared in ``include/snap.h``.
+PyTorch is used for device memory and streams (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``); nothing here falls back to a
+CPU or PyTorch implementation -- if the extension is missing, importing the
+library raises.
+
+Paper: CRIUgpu (arXiv 2502.16631): checkpoint copies a process's device state
+into host memory and restore copies it back (Sec. 3.1.1); the lock waits for
+in-flight work with a 10 s timeout (Sec. 3.1.1); incremental checkpointing is
+an optimisation Sec. 7 names.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsnap.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGET = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+FULL, INCREMENTAL = 0, 1
+REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
+
+# Every entry point declared in include/snap.h.
+EXPORTS = (
+    "snap_set_create", "snap_set_destroy", "snap_register", "snap_image_bytes",
+    "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_restore", "snap_verify",
+    "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
+    "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_autotune",
+    "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
+)
+
+
+class SnapError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _lib().snap_strerror(status).decode() if _LIB is not None else str(status)
+        super().__init__("%s: %s (%d)" % (what, msg, status) if what else "%s (%d)" % (msg, status))
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_uint64), ("timeout_ms", ctypes.c_uint32),
+                ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("ctas_per_sm", ctypes.c_uint32), ("stages", ctypes.c_uint32),
+                ("ring_bytes", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("state_bytes", ctypes.c_uint64), ("image_bytes", ctypes.c_uint64),
+                ("total_chunks", ctypes.c_uint64), ("dirty_chunks", ctypes.c_uint64),
+                ("mismatches", ctypes.c_uint64), ("generation", ctypes.c_uint64),
+                ("quiesce_ms", ctypes.c_double), ("hash_ms", ctypes.c_double),
+                ("diff_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_uint32), ("stages", ctypes.c_uint32),
+                ("piece_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("gbs", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def _lib():
+    """Load libsnap.so (building it in-tree first if sources changed)."""
+    global _LIB
+    if _LIB is None:
+        if _build.stale():
+            _build.build()
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        P = ctypes.POINTER
+        sig = {
+            "snap_set_create": [P(vp), P(Opts)],
+            "snap_set_destroy": [vp],
+            "snap_register": [vp, vp, u64],
+            "snap_image_bytes": [vp, i32, P(u64)],
+            "snap_host_alloc": [u64, P(vp)],
+            "snap_host_free": [vp],
+            "snap_checkpoint": [vp, vp, u64, i32, P(u64)],
+            "snap_restore": [vp, u64, vp],
+            "snap_verify": [vp, u64, vp, P(u64)],
+            "snap_apply_patch": [vp, u64, vp, u64],
+            "snap_committed_hashes": [vp, vp, u64, P(u64)],
+            "snap_last_stats": [vp, P(Stats)],
+            "snap_strerror": [i32],
+            "snap_plain_checkpoint": [vp, vp, u64],
+            "snap_plain_restore": [vp, u64, vp],
+            "snap_hash_chunks": [vp, u64, u64, vp, vp],
+            "snap_autotune": [vp, i32, vp, u64, P(Tuning)],
+            "snap_server_create": [P(vp), u64, u64, P(Opts)],
+            "snap_server_destroy": [vp],
+            "snap_server_submit": [vp, vp, i32, vp, u64, P(u64)],
+            "snap_server_wait": [vp, u64, u32, P(i32), P(Stats)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name == "snap_strerror" else ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    return _lib()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise SnapError(rc, what)
+    return rc
+
+
+def strerror(status: int) -> str:
+    return _lib().snap_strerror(status).decode()
+
+
+def _addr(x) -> int:
+    """Device/host address of a torch tensor, HostBuffer, numpy array or int."""
+    if isinstance(x, int):
+        return x
+    if isinstance(x, HostBuffer):
+        return x.ptr
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _nbytes(x) -> int:
+    if isinstance(x, HostBuffer):
+        return x.nbytes
+    if isinstance(x, np.ndarray):
+        return x.nbytes
+    if hasattr(x, "untyped_storage"):
+        return x.numel() * x.element_size()
+    raise TypeError("cannot size %r" % type(x))
+
+
+class HostBuffer:
+    """Pinned, device-mapped host memory from snap_host_alloc."""
+
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        _check(_lib().snap_host_alloc(nbytes, ctypes.byref(p)), "snap_host_alloc")
+        self.ptr = p.value
+        self.nbytes = nbytes
+        self.array = np.ctypeslib.as_array((ctypes.c_uint8 * nbytes).from_address(self.ptr))
+
+    def view(self, n: int | None = None) -> np.ndarray:
+        return self.array[: self.nbytes if n is None else n]
+
+    def close(self):
+        if self.ptr:
+            self.array = None
+            _lib().snap_host_free(self.ptr)
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Set:
+    """A set of registered device allocations (snap_set)."""
+
+    def __init__(self, chunk_bytes: int = 0, timeout_ms: int = 0, device: int = -1, stream=None,
+                 ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0):
+        o = Opts(chunk_bytes, timeout_ms, device, _stream_handle(stream), ctas_per_sm, stages, ring_bytes)
+        h = ctypes.c_void_p()
+        _check(_lib().snap_set_create(ctypes.byref(h), ctypes.byref(o)), "snap_set_create")
+        self.h = h.value
+        self.tensors = []
+
+    def close(self):
+        if self.h:
+            _lib().snap_set_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, t, nbytes: int | None = None) -> int:
+        """Register a device tensor (or a raw device address with nbytes)."""
+        if nbytes is None:
+            nbytes = _nbytes(t)
+        if not isinstance(t, int):
+            self.tensors.append(t)
+        return _check(_lib().snap_register(self.h, _addr(t), nbytes), "snap_register")
+
+    def image_bytes(self, mode: int = FULL) -> int:
+        v = ctypes.c_uint64()
+        _check(_lib().snap_image_bytes(self.h, mode, ctypes.byref(v)), "snap_image_bytes")
+        return v.value
+
+    def checkpoint(self, image, mode: int = FULL, cap: int | None = None) -> int:
+        used = ctypes.c_uint64()
+        _check(_lib().snap_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+                                      ctypes.byref(used)), "snap_checkpoint")
+        return used.value
+
+    def checkpoint_status(self, image, mode: int = FULL, cap: int | None = None):
+        used = ctypes.c_uint64()
+        rc = _lib().snap_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+                                    ctypes.byref(used))
+        return rc, used.value
+
+    def restore(self, image, nbytes: int | None = None) -> None:
+        _check(self.restore_status(image, nbytes), "snap_restore")
+
+    def restore_status(self, image, nbytes: int | None = None) -> int:
+        return _lib().snap_restore(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h)
+
+    def verify(self, image, nbytes: int | None = None) -> int:
+        bad = ctypes.c_uint64()
+        _check(_lib().snap_verify(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+                                  ctypes.byref(bad)), "snap_verify")
+        return bad.value
+
+    def committed_hashes(self, n: int) -> tuple[np.ndarray, int]:
+        out = np.zeros(max(n, 1), dtype=np.uint32)
+        gen = ctypes.c_uint64()
+        _check(_lib().snap_committed_hashes(self.h, out.ctypes.data, n, ctypes.byref(gen)),
+               "snap_committed_hashes")
+        return out[:n], gen.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(_lib().snap_last_stats(self.h, ctypes.byref(s)), "snap_last_stats")
+        return s.as_dict()
+
+    def plain_checkpoint(self, image, cap: int | None = None) -> None:
+        _check(_lib().snap_plain_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap),
+               "snap_plain_checkpoint")
+
+    def plain_restore(self, image, nbytes: int | None = None) -> None:
+        _check(_lib().snap_plain_restore(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h),
+               "snap_plain_restore")
+
+    def autotune(self, mode: int = INCREMENTAL, image=None) -> dict:
+        t = Tuning()
+        _check(_lib().snap_autotune(self.h, mode, _addr(image) if image is not None else None,
+                                    _nbytes(image) if image is not None else 0, ctypes.byref(t)),
+               "snap_autotune")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+
+def apply_patch(base, patch, base_bytes: int | None = None, patch_bytes: int | None = None) -> None:
+    """Merge `patch` into the full image `base` in place (host memory)."""
+    _check(apply_patch_status(base, patch, base_bytes, patch_bytes), "snap_apply_patch")
+
+
+def apply_patch_status(base, patch, base_bytes=None, patch_bytes=None) -> int:
+    return _lib().snap_apply_patch(_addr(base), _nbytes(base) if base_bytes is None else base_bytes,
+                                   _addr(patch), _nbytes(patch) if patch_bytes is None else patch_bytes)
+
+
+def hash_chunks(dev_tensor, chunk_bytes: int, out, nbytes: int | None = None, stream=None) -> None:
+    """CRC-32C of every chunk of a device buffer into the device array `out`."""
+    n = _nbytes(dev_tensor) if nbytes is None else nbytes
+    _check(_lib().snap_hash_chunks(_addr(dev_tensor), n, chunk_bytes, _addr(out), _stream_handle(stream)),
+           "snap_hash_chunks")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Server:
+    """Serving loop over tenant sets (snap_server)."""
+
+    def __init__(self, pinned_budget: int, hbm_budget: int, chunk_bytes: int = 0, timeout_ms: int = 0,
+                 device: int = -1, ring_bytes: int = 0):
+        o = Opts(chunk_bytes, timeout_ms, device, None, 0, 0, ring_bytes)
+        h = ctypes.c_void_p()
+        _check(_lib().snap_server_create(ctypes.byref(h), pinned_budget, hbm_budget, ctypes.byref(o)),
+               "snap_server_create")
+        self.h = h.value
+
+    def close(self):
+        if self.h:
+            _lib().snap_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, tenant: Set, kind: int, image, cap: int | None = None) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib().snap_server_submit(self.h, tenant.h, kind, _addr(image),
+                                         _nbytes(image) if cap is None else cap, ctypes.byref(t)),
+               "snap_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        st = ctypes.c_int()
+        s = Stats()
+        rc = _lib().snap_server_wait(self.h, ticket, timeout_ms, ctypes.byref(st), ctypes.byref(s))
+        return rc, st.value, s.as_dict()

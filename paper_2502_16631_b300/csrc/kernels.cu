@@ -76,7 +76,7 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 // Bounded wait for the completion of phase `parity` of the mbarrier at a.
-__device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity)
+__device__ __noinline__ bool mbar_wait_lane(uint32_t a, uint32_t parity)
 {
     if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = global_ns();
@@ -85,6 +85,13 @@ __device__ __noinline__ bool mbar_wait(uint32_t a, uint32_t parity)
         if (global_ns() - t0 > kWaitNs) return false;
         __nanosleep(128);
     }
+}
+// Warp-wide: every lane waits, and the warp agrees on the outcome so that
+// control flow never diverges around the full-mask shuffles that follow.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity)
+{
+    const bool ok = mbar_wait_lane(a, parity);
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 __device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
 {
@@ -281,6 +288,9 @@ __device__ bool gather_chunk_int(WarpCtx &w, const uint8_t *src, uint32_t L, uin
     uint32_t e = 0;  // end of this lane's last hashed piece
 
     const uint32_t pre = nst < (uint32_t)w.stages ? nst : (uint32_t)w.stages;
+    // the buffers were last touched through the generic proxy (reads, or
+    // cp.async writes of a hashed chunk): order that before the TMA writes
+    fence_proxy_async();
     for (uint32_t k = 0; k < pre; ++k) int_issue(w, src, L, k);
     for (uint32_t k = 0; k < nst; ++k) {
         const uint32_t g = w.consumed;
@@ -415,7 +425,9 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
         if (lane == 0) t = atomicAdd(cursor, 1ull);
         t = __shfl_sync(0xFFFFFFFFu, t, 0);
         if (t >= total) break;
-        if (*reinterpret_cast<volatile unsigned long long *>(&kres->err)) break;
+        // another warp gave up: stop (lane 0 reads, the warp follows it)
+        unsigned long long err = lane == 0 ? *reinterpret_cast<volatile unsigned long long *>(&kres->err) : 0ull;
+        if (__shfl_sync(0xFFFFFFFFu, err, 0)) break;
         int j = 0;
         while (j + 1 < n_jobs && prefix[j + 1] <= t) ++j;
         const Job &jb = jobs[j];

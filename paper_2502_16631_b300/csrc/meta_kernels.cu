@@ -15,8 +15,10 @@ __device__ __forceinline__ uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint
 // Block k writes allocation k's 32-byte record {bytes, n, data_off, 0} and
 // zeroes the padding between its hash array and its data.  (The hashes, the
 // data and the data padding are written by the gather tiles.)
-__global__ void k_full_meta(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C, uint8_t *image)
+__global__ void k_full_meta(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C,
+                            const CallParams *cp)
 {
+    uint8_t *image = cp->image;
     const uint64_t k = blockIdx.x;
     if (k >= n_allocs) return;
     const AllocDesc a = allocs[k];
@@ -35,11 +37,11 @@ __global__ void k_full_meta(const AllocDesc *__restrict__ allocs, uint64_t n_all
     // a zero-byte allocation has no chunk tile to pad its (empty) data
 }
 
-cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, uint8_t *image,
+cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, const CallParams *cp,
                              cudaStream_t st)
 {
     if (n_allocs == 0) return cudaSuccess;
-    k_full_meta<<<(unsigned)n_allocs, 128, 0, st>>>(allocs, n_allocs, C, image);
+    k_full_meta<<<(unsigned)n_allocs, 128, 0, st>>>(allocs, n_allocs, C, cp);
     return cudaGetLastError();
 }
 
@@ -140,8 +142,9 @@ __device__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t n, uint64_t key)
 
 __global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C,
                                const uint32_t *__restrict__ dlist, uint64_t *patch_rec, uint64_t *patch_data,
-                               uint64_t *dstart, uint64_t cap, Result *res)
+                               uint64_t *dstart, const CallParams *cp, Result *res)
 {
+    const uint64_t cap = cp->cap;
     const unsigned long long nd_all = res->n_dirty;
     unsigned long long carry = 64;
     for (uint64_t base = 0; base < n_allocs; base += kDiffBlock) {
@@ -180,10 +183,10 @@ __global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t n_
 }
 
 cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, const uint32_t *dlist,
-                                uint64_t *patch_rec, uint64_t *patch_data, uint64_t *dstart, uint64_t cap,
+                                uint64_t *patch_rec, uint64_t *patch_data, uint64_t *dstart, const CallParams *cp,
                                 Result *res, cudaStream_t st)
 {
-    k_patch_layout<<<1, kDiffBlock, 0, st>>>(allocs, n_allocs, C, dlist, patch_rec, patch_data, dstart, cap, res);
+    k_patch_layout<<<1, kDiffBlock, 0, st>>>(allocs, n_allocs, C, dlist, patch_rec, patch_data, dstart, cp, res);
     return cudaGetLastError();
 }
 
@@ -192,9 +195,10 @@ cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint
 __global__ void k_patch_meta(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C,
                              const uint32_t *__restrict__ cur, const uint32_t *__restrict__ dlist,
                              const uint64_t *__restrict__ patch_rec, const uint64_t *__restrict__ patch_data,
-                             const uint64_t *__restrict__ dstart, const Result *res, uint8_t *image)
+                             const uint64_t *__restrict__ dstart, const Result *res, const CallParams *cp)
 {
     if (res->cap_exceeded) return;
+    uint8_t *image = cp->image;
     const uint64_t k = blockIdx.x;
     if (k >= n_allocs) return;
     const AllocDesc a = allocs[k];
@@ -220,11 +224,11 @@ __global__ void k_patch_meta(const AllocDesc *__restrict__ allocs, uint64_t n_al
 
 cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, const uint32_t *cur,
                               const uint32_t *dlist, const uint64_t *patch_rec, const uint64_t *patch_data,
-                              const uint64_t *dstart, const Result *res, uint8_t *image, cudaStream_t st)
+                              const uint64_t *dstart, const Result *res, const CallParams *cp, cudaStream_t st)
 {
     if (n_allocs == 0) return cudaSuccess;
     k_patch_meta<<<(unsigned)n_allocs, 256, 0, st>>>(allocs, n_allocs, C, cur, dlist, patch_rec, patch_data, dstart,
-                                                     res, image);
+                                                     res, cp);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,831 @@
+// Host runtime of libsnap: sets, image layout, quiesce ("lock", CRIUgpu
+// Sec. 3.1.1), graph-captured launch sequences, commit/rollback (Sec. 3.1:
+// on failure the previous state stands), restore validation (Sec. 4.4: the
+// target must match), the plain per-allocation copy form, and the
+// standalone chunk hasher.
+#include "snap.h"
+#include "snap_format.h"
+#include "snap_internal.h"
+#include "crc32c_gf2.h"
+#include "runtime_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <thread>
+
+using namespace snapk;
+
+namespace snapk {
+
+// ------------------------------------------------------------ small helpers
+static inline uint64_t up_page(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
+
+double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+bool fault_injected(const char *what)
+{
+    const char *f = std::getenv("SNAP_FAULT");
+    return f && std::strstr(f, what) != nullptr;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return SNAP_OK;
+    if (e == cudaErrorMemoryAllocation) return SNAP_ENOMEM;
+    if (std::getenv("SNAP_LOG")) fprintf(stderr, "libsnap: CUDA error %s\n", cudaGetErrorString(e));
+    return SNAP_ECUDA;
+}
+
+// Poll `ev` until complete or the deadline passes (bounded wait on the host).
+int wait_event(cudaEvent_t ev, double deadline_ms)
+{
+    int spins = 0;
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) return SNAP_OK;
+        if (q != cudaErrorNotReady) return cuda_status(q);
+        if (now_ms() > deadline_ms) return SNAP_ETIMEDOUT;
+        if (++spins < 2000) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Device-visible address of a host buffer if it is pinned and mapped.
+uint8_t *mapped_device_ptr(const void *host)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+    return static_cast<uint8_t *>(at.devicePointer);
+}
+
+void write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n, uint64_t total, uint64_t gen,
+                  uint64_t parent)
+{
+    uint8_t b[64];
+    std::memset(b, 0, sizeof b);
+    std::memcpy(b, SNAP_IMG_MAGIC, 8);
+    const uint32_t ver = SNAP_IMG_VERSION;
+    std::memcpy(b + 8, &ver, 4);
+    std::memcpy(b + 12, &flags, 4);
+    std::memcpy(b + 16, &C, 8);
+    std::memcpy(b + 24, &n, 8);
+    std::memcpy(b + 32, &total, 8);
+    std::memcpy(b + 40, &gen, 8);
+    std::memcpy(b + 48, &parent, 8);
+    const uint32_t crc = host_crc32c(b, 56);
+    std::memcpy(b + 56, &crc, 4);
+    std::memcpy(h, b, 64);
+}
+
+int parse_header(const uint8_t *img, uint64_t len, ImageHeader *h)
+{
+    if (!img || len < SNAP_IMG_HEADER_BYTES) return SNAP_EFORMAT;
+    uint8_t b[64];
+    std::memcpy(b, img, 64);
+    if (std::memcmp(b, SNAP_IMG_MAGIC, 8) != 0) return SNAP_EFORMAT;
+    uint32_t ver, crc, pad;
+    std::memcpy(&ver, b + 8, 4);
+    std::memcpy(&h->flags, b + 12, 4);
+    std::memcpy(&h->chunk_bytes, b + 16, 8);
+    std::memcpy(&h->n_allocs, b + 24, 8);
+    std::memcpy(&h->total, b + 32, 8);
+    std::memcpy(&h->generation, b + 40, 8);
+    std::memcpy(&h->parent, b + 48, 8);
+    std::memcpy(&crc, b + 56, 4);
+    std::memcpy(&pad, b + 60, 4);
+    if (ver != SNAP_IMG_VERSION || pad != 0 || crc != host_crc32c(b, 56)) return SNAP_EFORMAT;
+    if (!(h->flags & SNAP_IMG_FLAG_DEVICE_STATE) || (h->flags & ~3u)) return SNAP_EFORMAT;
+    if (h->chunk_bytes < 4096 || h->chunk_bytes % 4096 || h->chunk_bytes > (1ull << 30)) return SNAP_EFORMAT;
+    return SNAP_OK;
+}
+
+// Walk an image's records (full or patch) against the set's allocations,
+// collecting every chunk hash into `hashes` (global chunk order).  For a full
+// image also checks that every data offset is where the layout puts it.
+int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes)
+{
+    if (h.chunk_bytes != s->C) return SNAP_EMISMATCH;
+    if (h.n_allocs != s->allocs.size()) return SNAP_EMISMATCH;
+    if (h.total != s->total_bytes) return SNAP_EMISMATCH;
+    const bool patch = (h.flags & SNAP_IMG_FLAG_INCREMENTAL) != 0;
+    uint64_t off = SNAP_IMG_HEADER_BYTES;
+    for (size_t k = 0; k < s->allocs.size(); ++k) {
+        const AllocDesc &a = s->desc[k];
+        if (off + 32 > len) return SNAP_EFORMAT;
+        uint64_t rec[4];
+        std::memcpy(rec, img + off, 32);
+        if (rec[0] != a.bytes) return SNAP_EMISMATCH;
+        const uint64_t nk = (a.bytes + s->C - 1) / s->C;
+        if (rec[1] != nk || rec[3] != 0) return SNAP_EFORMAT;
+        if (nk > (len - off - 32) / 4) return SNAP_EFORMAT;
+        if (hashes) std::memcpy(hashes + a.chunk0, img + off + 32, 4 * nk);
+        if (!patch) {
+            if (rec[2] != a.data_off || off != a.rec_off) return SNAP_EFORMAT;
+            if (a.data_off > len || a.bytes > len - a.data_off) return SNAP_EFORMAT;
+            off = up_page(a.data_off + a.bytes);
+        } else {
+            if (off + 36 + 4 * nk > len) return SNAP_EFORMAT;
+            uint32_t nd;
+            std::memcpy(&nd, img + off + 32 + 4 * nk, 4);
+            if (nd > nk || off + 36 + 4 * nk + 4ull * nd > len) return SNAP_EFORMAT;
+            if (rec[2] != up_page(off + 36 + 4 * nk + 4ull * nd)) return SNAP_EFORMAT;
+            uint64_t d = rec[2];
+            int64_t last = -1;
+            for (uint32_t j = 0; j < nd; ++j) {
+                uint32_t i;
+                std::memcpy(&i, img + off + 36 + 4 * nk + 4ull * j, 4);
+                if (i >= nk || (int64_t)i <= last) return SNAP_EFORMAT;
+                last = i;
+                const uint64_t L = std::min<uint64_t>(s->C, a.bytes - (uint64_t)i * s->C);
+                d += up_page(L);
+            }
+            off = d;
+        }
+    }
+    if (off > len) return SNAP_EFORMAT;
+    return SNAP_OK;
+}
+
+// ------------------------------------------------------------- set layout
+// Device arrays are (re)built lazily after registration changes.
+static void free_device(snap_set_s *s)
+{
+    for (auto &g : s->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
+    cudaFree(s->d_allocs);
+    cudaFree(s->d_hash[0]);
+    cudaFree(s->d_hash[1]);
+    cudaFree(s->d_cmp);
+    cudaFree(s->d_blockcnt);
+    cudaFree(s->d_blockoff);
+    cudaFree(s->d_dlist);
+    cudaFree(s->d_patch_rec);
+    cudaFree(s->d_patch_data);
+    cudaFree(s->d_dstart);
+    cudaFreeHost(s->h_hash_stage);
+    s->d_allocs = nullptr;
+    s->d_hash[0] = s->d_hash[1] = s->d_cmp = s->d_dlist = nullptr;
+    s->d_blockcnt = nullptr;
+    s->d_blockoff = nullptr;
+    s->d_patch_rec = s->d_patch_data = s->d_dstart = nullptr;
+    s->h_hash_stage = nullptr;
+}
+
+static int build_layout(snap_set_s *s)
+{
+    if (!s->layout_dirty) return SNAP_OK;
+    free_device(s);
+    s->has_base = false;
+    const uint64_t C = s->C;
+    s->desc.resize(s->allocs.size());
+    uint64_t off = SNAP_IMG_HEADER_BYTES, chunk = 0, state = 0;
+    for (size_t k = 0; k < s->allocs.size(); ++k) {
+        AllocDesc &a = s->desc[k];
+        a.ptr = (uint64_t)(uintptr_t)s->allocs[k].ptr;
+        a.bytes = s->allocs[k].bytes;
+        const uint64_t nk = (a.bytes + C - 1) / C;
+        a.chunk0 = chunk;
+        a.rec_off = off;
+        a.data_off = up_page(off + 32 + 4 * nk);
+        a.state_off = state;
+        off = up_page(a.data_off + a.bytes);
+        chunk += nk;
+        state += a.bytes;
+    }
+    s->n_chunks = chunk;
+    s->total_bytes = state;
+    s->full_bytes = off;
+    if (chunk > 0xFFFFFFFFull) return SNAP_EINVAL;  // dirty lists hold u32 chunk indices
+    // patch upper bound: full image + per allocation the dirty count, index list and a page
+    s->patch_bound = off;
+    for (size_t k = 0; k < s->allocs.size(); ++k) s->patch_bound += 4096 + 4 + 4 * ((s->desc[k].bytes + C - 1) / C);
+
+    const size_t na = std::max<size_t>(1, s->desc.size());
+    const size_t nc = std::max<uint64_t>(1, chunk);
+    const size_t nb = (nc + kDiffBlock - 1) / kDiffBlock;
+    if (fault_injected("hash_alloc")) return SNAP_ENOMEM;
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void **p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
+    al((void **)&s->d_allocs, na * sizeof(AllocDesc));
+    al((void **)&s->d_hash[0], nc * 4);
+    al((void **)&s->d_hash[1], nc * 4);
+    al((void **)&s->d_cmp, nc * 4);
+    al((void **)&s->d_blockcnt, nb * sizeof(unsigned int));
+    al((void **)&s->d_blockoff, nb * sizeof(unsigned long long));
+    al((void **)&s->d_dlist, nc * 4);
+    al((void **)&s->d_patch_rec, na * 8);
+    al((void **)&s->d_patch_data, na * 8);
+    al((void **)&s->d_dstart, (na + 1) * 8);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_hash_stage, nc * 4, cudaHostAllocDefault);
+    if (e == cudaSuccess && !s->desc.empty())
+        e = cudaMemcpy(s->d_allocs, s->desc.data(), s->desc.size() * sizeof(AllocDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_device(s);
+        return cuda_status(e);
+    }
+    s->layout_dirty = false;
+    return SNAP_OK;
+}
+
+// ------------------------------------------------------------ call plumbing
+struct BusyGuard {
+    snap_set_s *s;
+    bool ok;
+    explicit BusyGuard(snap_set_s *s_) : s(s_) { ok = !s->busy.exchange(true); }
+    ~BusyGuard() { if (ok) s->busy.store(false); }
+};
+
+// A previous call that timed out may still be running on the library
+// stream; wait for it (bounded) before touching shared buffers again.
+static int settle(snap_set_s *s, double deadline)
+{
+    if (!s->in_flight) return SNAP_OK;
+    const int rc = wait_event(s->ev[EV_END], deadline);
+    if (rc == SNAP_OK) s->in_flight = false;
+    return rc == SNAP_ETIMEDOUT ? SNAP_EBUSY : rc;
+}
+
+// Quiesce the caller's stream: every operation queued on it must finish
+// before the snapshot reads device memory (the lock action, Sec. 3.1.1).
+static int quiesce(snap_set_s *s, double deadline)
+{
+    cudaError_t e = cudaEventRecord(s->ev_quiesce, s->user_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return wait_event(s->ev_quiesce, deadline);
+}
+
+TileShape shape_for(const snap_set_s *s, int kind)
+{
+    TileShape sh = s->shape[kind];
+    return sh;
+}
+
+// Capture (once) and launch the graph for `kind`; parity selects which hash
+// table is "current".
+static int run_graph(snap_set_s *s, int kind, int parity, const std::function<cudaError_t(cudaStream_t)> &body)
+{
+    GraphEntry *g = nullptr;
+    for (auto &x : s->graphs)
+        if (x.kind == kind && x.parity == parity) g = &x;
+    if (!g) {
+        if (fault_injected("graph")) return SNAP_ENOMEM;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaError_t eb = body(s->st);
+        e = cudaStreamEndCapture(s->st, &graph);
+        if (eb != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_status(eb != cudaSuccess ? eb : e);
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e);
+        s->graphs.push_back(GraphEntry{kind, parity, exec});
+        g = &s->graphs.back();
+    }
+    return cuda_status(cudaGraphLaunch(g->exec, s->st));
+}
+
+// Fill the per-call block's header part (cursors, result, params).
+static void reset_call(snap_set_s *s, uint8_t *image, uint64_t cap)
+{
+    CallBlock &cb = *s->h_cb;
+    std::memset(&cb, 0, offsetof(CallBlock, jobs));
+    cb.res.first_bad = ~0ull;
+    cb.cp.image = image;
+    cb.cp.cap = cap;
+}
+
+static Job base_job(const snap_set_s *s, uint32_t op)
+{
+    Job j{};
+    j.allocs = s->d_allocs;
+    j.n_allocs = s->desc.size();
+    j.chunk_bytes = s->C;
+    j.tile_begin = 0;
+    j.n_tiles = s->n_chunks;
+    j.op = op;
+    j.layout = LAYOUT_IMAGE;
+    j.res = &s->d_cb->res;
+    return j;
+}
+
+// Enqueue: copy the call block in, then body, then the result out.
+static cudaError_t enqueue_prologue(snap_set_s *s, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, sizeof(CallBlock), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_BEGIN], st);
+    return e;
+}
+static cudaError_t enqueue_epilogue(snap_set_s *s, cudaStream_t st)
+{
+    cudaError_t e = cudaEventRecord(s->ev[EV_COPY_END], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, st);
+    return e;
+}
+
+static float ev_ms(snap_set_s *s, int a, int b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev[a], s->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+// Launch the graph, wait for it with the deadline, check the kernels' flags.
+static int finish(snap_set_s *s, double deadline)
+{
+    cudaError_t e = cudaEventRecord(s->ev[EV_END], s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rc = wait_event(s->ev[EV_END], deadline);
+    if (rc == SNAP_ETIMEDOUT) {
+        s->in_flight = true;
+        return rc;
+    }
+    if (rc) return rc;
+    if (s->h_res->err) return SNAP_ECUDA;
+    return SNAP_OK;
+}
+
+}  // namespace snapk
+
+// ===================================================================== ABI
+extern "C" {
+
+const char *snap_strerror(int st)
+{
+    switch (st) {
+    case SNAP_OK: return "ok";
+    case SNAP_EINVAL: return "invalid argument";
+    case SNAP_ENOMEM: return "out of memory";
+    case SNAP_ECUDA: return "CUDA error";
+    case SNAP_ETIMEDOUT: return "timed out";
+    case SNAP_ENOBASE: return "no committed base for an incremental checkpoint";
+    case SNAP_EFORMAT: return "malformed image";
+    case SNAP_EMISMATCH: return "image does not match the set";
+    case SNAP_EBUSY: return "set busy";
+    case SNAP_EBUDGET: return "request exceeds the server budgets";
+    default: return "unknown status";
+    }
+}
+
+int snap_host_alloc(uint64_t bytes, void **out)
+{
+    if (!out || bytes == 0) return SNAP_EINVAL;
+    *out = nullptr;
+    if (fault_injected("pinned_alloc")) return SNAP_ENOMEM;
+    cudaError_t e = cudaHostAlloc(out, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return SNAP_ENOMEM;
+    }
+    return SNAP_OK;
+}
+
+int snap_host_free(void *p)
+{
+    if (!p) return SNAP_OK;
+    return cuda_status(cudaFreeHost(p));
+}
+
+int snap_set_create(snap_set *out, const snap_opts *o)
+{
+    if (!out) return SNAP_EINVAL;
+    *out = nullptr;
+    snap_opts opt{};
+    if (o) opt = *o;
+    if (opt.chunk_bytes == 0) opt.chunk_bytes = 65536;
+    if (opt.chunk_bytes < 4096 || opt.chunk_bytes % 4096 || opt.chunk_bytes > (16u << 20)) return SNAP_EINVAL;
+    if (opt.timeout_ms == 0) opt.timeout_ms = 10000;
+    if (opt.ring_bytes == 0) opt.ring_bytes = 4ull << 30;
+    int dev = o ? opt.device : -1;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return SNAP_ECUDA;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) return SNAP_EINVAL;
+    if (cudaSetDevice(dev) != cudaSuccess) return SNAP_ECUDA;
+    auto *s = new (std::nothrow) snap_set_s();
+    if (!s) return SNAP_ENOMEM;
+    s->device = dev;
+    s->C = opt.chunk_bytes;
+    s->timeout_ms = opt.timeout_ms;
+    s->user_stream = static_cast<cudaStream_t>(opt.stream);
+    s->opts = opt;
+    cudaDeviceProp prop{};
+    cudaError_t e = cudaGetDeviceProperties(&prop, dev);
+    s->sms = prop.multiProcessorCount;
+    std::snprintf(s->gpu_name, sizeof s->gpu_name, "%s", prop.name);
+    if (e == cudaSuccess) e = init_tile_kernel();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_quiesce, cudaEventDisableTiming);
+    for (int i = 0; i < EV_COUNT && e == cudaSuccess; ++i) e = cudaEventCreate(&s->ev[i]);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_cb, sizeof(CallBlock));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_cb, sizeof(CallBlock), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_res, sizeof(Result), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        snap_set_destroy(s);
+        return cuda_status(e);
+    }
+    default_shapes(s);
+    *out = s;
+    return SNAP_OK;
+}
+
+int snap_set_destroy(snap_set s)
+{
+    if (!s) return SNAP_EINVAL;
+    cudaSetDevice(s->device);
+    if (s->st) cudaStreamSynchronize(s->st);
+    free_device(s);
+    ring_free(s);
+    cudaFree(s->d_cb);
+    cudaFreeHost(s->h_cb);
+    cudaFreeHost(s->h_res);
+    if (s->ev_quiesce) cudaEventDestroy(s->ev_quiesce);
+    for (int i = 0; i < EV_COUNT; ++i) if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+    return SNAP_OK;
+}
+
+int snap_register(snap_set s, void *dptr, uint64_t bytes)
+{
+    if (!s) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    if (bytes && !dptr) return SNAP_EINVAL;
+    if ((uintptr_t)dptr & 15u) return SNAP_EINVAL;
+    if (s->allocs.size() >= (size_t)INT32_MAX) return SNAP_EINVAL;
+    if (bytes) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, dptr) != cudaSuccess) {
+            cudaGetLastError();
+            return SNAP_EINVAL;
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return SNAP_EINVAL;
+        if (at.device != s->device) return SNAP_EINVAL;
+    }
+    s->allocs.push_back(HostAlloc{dptr, bytes});
+    s->layout_dirty = true;
+    s->has_base = false;
+    return (int)(s->allocs.size() - 1);
+}
+
+int snap_image_bytes(snap_set s, int mode, uint64_t *out)
+{
+    if (!s || !out) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const int rc = build_layout(s);
+    if (rc) return rc;
+    if (mode == SNAP_FULL) *out = s->full_bytes;
+    else if (mode == SNAP_INCREMENTAL) *out = s->patch_bound;
+    else return SNAP_EINVAL;
+    return SNAP_OK;
+}
+
+int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image || ((uintptr_t)host_image & 15u)) return SNAP_EINVAL;
+    if (mode != SNAP_FULL && mode != SNAP_INCREMENTAL) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    int rc = settle(s, deadline);
+    if (rc) return rc;
+    rc = build_layout(s);
+    if (rc) return rc;
+    if (mode == SNAP_INCREMENTAL && !s->has_base) return SNAP_ENOBASE;
+    if (mode == SNAP_FULL && cap < s->full_bytes) return SNAP_EINVAL;
+    if (mode == SNAP_INCREMENTAL && cap < SNAP_IMG_HEADER_BYTES) return SNAP_EINVAL;
+
+    uint8_t *dimg = mapped_device_ptr(host_image);
+    rc = quiesce(s, deadline);
+    if (rc) return rc;
+    const double tq = now_ms();
+    if (!dimg) return ring_checkpoint(s, static_cast<uint8_t *>(host_image), cap, mode, used, t0, tq, deadline);
+
+    const int cur = 1 - s->prev_idx;
+    const uint64_t gen = s->has_base ? s->next_gen : s->next_gen;
+    reset_call(s, dimg, cap);
+    snap_stats st{};
+    if (mode == SNAP_FULL) {
+        Job j = base_job(s, OP_GATHER);
+        j.host = dimg;
+        j.hash_out = s->d_hash[cur];
+        s->h_cb->jobs[0] = j;
+        const TileShape sh = s->shape[SHAPE_GATHER];
+        const CombineConsts cc = make_combine_consts(s->C, sh.piece);
+        rc = run_graph(s, GK_FULL, cur, [&](cudaStream_t q) {
+            cudaError_t e = enqueue_prologue(s, q);
+            if (e == cudaSuccess) e = launch_full_meta(s->d_allocs, s->desc.size(), s->C, &s->d_cb->cp, q);
+            if (e == cudaSuccess && s->n_chunks)
+                e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, sh, &s->d_cb->res, q);
+            if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+            return e;
+        });
+        if (rc == SNAP_OK) rc = finish(s, deadline);
+        if (rc) return rc;
+        write_header(static_cast<uint8_t *>(host_image), SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(),
+                     s->total_bytes, gen, 0);
+        *used = s->full_bytes;
+        st.image_bytes = s->full_bytes;
+        st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+        st.dirty_chunks = s->n_chunks;
+    } else {
+        Job jh = base_job(s, OP_HASH);
+        jh.hash_out = s->d_hash[cur];
+        Job jg = base_job(s, OP_GATHER_DIRTY);
+        jg.host = dimg;
+        jg.tile_list = s->d_dlist;
+        jg.n_tiles_dev = &s->d_cb->res.n_dirty;
+        jg.patch_data = s->d_patch_data;
+        jg.dstart = s->d_dstart;
+        jg.cap_exceeded = &s->d_cb->res.cap_exceeded;
+        s->h_cb->jobs[0] = jh;
+        s->h_cb->jobs[1] = jg;
+        const TileShape shh = s->shape[SHAPE_HASH];
+        const TileShape shg = s->shape[SHAPE_GATHER];
+        const CombineConsts cch = make_combine_consts(s->C, shh.piece);
+        const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
+        const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
+        rc = run_graph(s, GK_INCR, cur, [&](cudaStream_t q) {
+            cudaError_t e = enqueue_prologue(s, q);
+            if (e == cudaSuccess && s->n_chunks)
+                e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cch, shh, &s->d_cb->res, q);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_HASH_END], q);
+            if (e == cudaSuccess)
+                e = launch_diff(curp, prevp, s->n_chunks, s->d_blockcnt, s->d_blockoff, s->d_dlist, &s->d_cb->res, q);
+            if (e == cudaSuccess)
+                e = launch_patch_layout(s->d_allocs, s->desc.size(), s->C, s->d_dlist, s->d_patch_rec,
+                                        s->d_patch_data, s->d_dstart, &s->d_cb->cp, &s->d_cb->res, q);
+            if (e == cudaSuccess)
+                e = launch_patch_meta(s->d_allocs, s->desc.size(), s->C, curp, s->d_dlist, s->d_patch_rec,
+                                      s->d_patch_data, s->d_dstart, &s->d_cb->res, &s->d_cb->cp, q);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_DIFF_END], q);
+            if (e == cudaSuccess && s->n_chunks)
+                e = launch_tiles(s->d_cb->jobs + 1, 1, &s->d_cb->cursor[1], ccg, shg, &s->d_cb->res, q);
+            if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+            return e;
+        });
+        if (rc == SNAP_OK) rc = finish(s, deadline);
+        if (rc) return rc;
+        if (s->h_res->cap_exceeded) return SNAP_EINVAL;
+        write_header(static_cast<uint8_t *>(host_image), SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C,
+                     s->desc.size(), s->total_bytes, gen, s->base_gen);
+        *used = s->h_res->patch_bytes;
+        st.image_bytes = s->h_res->patch_bytes;
+        st.dirty_chunks = s->h_res->n_dirty;
+        st.hash_ms = ev_ms(s, EV_BEGIN, EV_HASH_END);
+        st.diff_ms = ev_ms(s, EV_HASH_END, EV_DIFF_END);
+        st.copy_ms = ev_ms(s, EV_DIFF_END, EV_COPY_END);
+    }
+    // commit (Sec. 3.1: only a completed checkpoint replaces the base)
+    s->prev_idx = cur;
+    s->has_base = true;
+    s->base_gen = gen;
+    s->next_gen = gen + 1;
+    st.state_bytes = s->total_bytes;
+    st.total_chunks = s->n_chunks;
+    st.generation = gen;
+    st.quiesce_ms = tq - t0;
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image || ((uintptr_t)host_image & 15u)) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    int rc = settle(s, deadline);
+    if (rc) return rc;
+    rc = build_layout(s);
+    if (rc) return rc;
+    const uint8_t *img = static_cast<const uint8_t *>(host_image);
+    ImageHeader h{};
+    rc = parse_header(img, bytes, &h);
+    if (rc) return rc;
+    if (h.flags & SNAP_IMG_FLAG_INCREMENTAL) return SNAP_EFORMAT;  // merge patches first
+    if (bytes < s->full_bytes && h.n_allocs == s->desc.size() && h.chunk_bytes == s->C && h.total == s->total_bytes)
+        return SNAP_EFORMAT;
+    rc = walk_records(s, img, bytes, h, s->h_hash_stage);
+    if (rc) return rc;
+    uint8_t *dimg = mapped_device_ptr(host_image);
+    rc = quiesce(s, deadline);
+    if (rc) return rc;
+    const double tq = now_ms();
+    if (!dimg) return ring_restore(s, img, bytes, h, t0, tq, deadline);
+
+    const int cur = 1 - s->prev_idx;
+    reset_call(s, dimg, bytes);
+    Job j = base_job(s, OP_SCATTER);
+    j.host = dimg;
+    s->h_cb->jobs[0] = j;
+    const TileShape sh = s->shape[SHAPE_SCATTER];
+    const CombineConsts cc = make_combine_consts(s->C, sh.piece);
+    rc = run_graph(s, GK_RESTORE, cur, [&](cudaStream_t q) {
+        cudaError_t e = enqueue_prologue(s, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = cudaMemcpyAsync(s->d_hash[cur], s->h_hash_stage, s->n_chunks * 4, cudaMemcpyHostToDevice, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, sh, &s->d_cb->res, q);
+        if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+        return e;
+    });
+    if (rc == SNAP_OK) rc = finish(s, deadline);
+    if (rc) return rc;
+    s->prev_idx = cur;
+    s->has_base = true;
+    s->base_gen = h.generation;
+    s->next_gen = h.generation + 1;
+    snap_stats st{};
+    st.state_bytes = s->total_bytes;
+    st.image_bytes = s->full_bytes;
+    st.total_chunks = s->n_chunks;
+    st.generation = h.generation;
+    st.quiesce_ms = tq - t0;
+    st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_mismatch)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image || !n_mismatch) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    int rc = settle(s, deadline);
+    if (rc) return rc;
+    rc = build_layout(s);
+    if (rc) return rc;
+    const uint8_t *img = static_cast<const uint8_t *>(host_image);
+    ImageHeader h{};
+    rc = parse_header(img, bytes, &h);
+    if (rc) return rc;
+    rc = walk_records(s, img, bytes, h, s->h_hash_stage);
+    if (rc) return rc;
+    rc = quiesce(s, deadline);
+    if (rc) return rc;
+    const double tq = now_ms();
+    reset_call(s, nullptr, 0);
+    Job j = base_job(s, OP_VERIFY);
+    j.hash_cmp = s->d_cmp;
+    s->h_cb->jobs[0] = j;
+    const TileShape sh = s->shape[SHAPE_HASH];
+    const CombineConsts cc = make_combine_consts(s->C, sh.piece);
+    rc = run_graph(s, GK_VERIFY, 0, [&](cudaStream_t q) {
+        cudaError_t e = enqueue_prologue(s, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = cudaMemcpyAsync(s->d_cmp, s->h_hash_stage, s->n_chunks * 4, cudaMemcpyHostToDevice, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, sh, &s->d_cb->res, q);
+        if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+        return e;
+    });
+    if (rc == SNAP_OK) rc = finish(s, deadline);
+    if (rc) return rc;
+    *n_mismatch = s->h_res->mismatches;
+    snap_stats st{};
+    st.state_bytes = s->total_bytes;
+    st.total_chunks = s->n_chunks;
+    st.mismatches = s->h_res->mismatches;
+    st.generation = h.generation;
+    st.quiesce_ms = tq - t0;
+    st.hash_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+int snap_committed_hashes(snap_set s, uint32_t *out, uint64_t n, uint64_t *generation)
+{
+    if (!s || (!out && n)) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    if (!s->has_base || s->layout_dirty) return SNAP_ENOBASE;
+    if (n < s->n_chunks) return SNAP_EINVAL;
+    if (s->n_chunks) {
+        cudaError_t e = cudaMemcpy(out, s->d_hash[s->prev_idx], s->n_chunks * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (generation) *generation = s->base_gen;
+    return SNAP_OK;
+}
+
+int snap_last_stats(snap_set s, snap_stats *out)
+{
+    if (!s || !out) return SNAP_EINVAL;
+    *out = s->last;
+    return SNAP_OK;
+}
+
+int snap_apply_patch(void *base_image, uint64_t base_bytes, const void *patch, uint64_t patch_bytes)
+{
+    return apply_patch_host(static_cast<uint8_t *>(base_image), base_bytes, static_cast<const uint8_t *>(patch),
+                            patch_bytes);
+}
+
+// ------------------------------------------------------------- plain form
+int snap_plain_checkpoint(snap_set s, void *host_image, uint64_t cap)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    int rc = settle(s, deadline);
+    if (rc) return rc;
+    rc = build_layout(s);
+    if (rc) return rc;
+    if (cap < s->full_bytes) return SNAP_EINVAL;
+    rc = quiesce(s, deadline);
+    if (rc) return rc;
+    uint8_t *img = static_cast<uint8_t *>(host_image);
+    cudaError_t e = cudaEventRecord(s->ev[EV_BEGIN], s->st);
+    for (size_t k = 0; k < s->desc.size() && e == cudaSuccess; ++k)
+        if (s->desc[k].bytes)
+            e = cudaMemcpyAsync(img + s->desc[k].data_off, s->allocs[k].ptr, s->desc[k].bytes, cudaMemcpyDeviceToHost,
+                                s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_COPY_END], s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaEventRecord(s->ev[EV_END], s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = wait_event(s->ev[EV_END], deadline);
+    if (rc == SNAP_ETIMEDOUT) s->in_flight = true;
+    if (rc) return rc;
+    snap_stats st{};
+    st.state_bytes = s->total_bytes;
+    st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    int rc = settle(s, deadline);
+    if (rc) return rc;
+    rc = build_layout(s);
+    if (rc) return rc;
+    if (bytes < s->full_bytes) return SNAP_EINVAL;
+    rc = quiesce(s, deadline);
+    if (rc) return rc;
+    const uint8_t *img = static_cast<const uint8_t *>(host_image);
+    cudaError_t e = cudaEventRecord(s->ev[EV_BEGIN], s->st);
+    for (size_t k = 0; k < s->desc.size() && e == cudaSuccess; ++k)
+        if (s->desc[k].bytes)
+            e = cudaMemcpyAsync(s->allocs[k].ptr, img + s->desc[k].data_off, s->desc[k].bytes, cudaMemcpyHostToDevice,
+                                s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_COPY_END], s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_END], s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = wait_event(s->ev[EV_END], deadline);
+    if (rc == SNAP_ETIMEDOUT) s->in_flight = true;
+    if (rc) return rc;
+    snap_stats st{};
+    st.state_bytes = s->total_bytes;
+    st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Host-side state of libsnap (runtime.cu, ring.cu, tune.cu, server.cu).
+#pragma once
+#include "snap.h"
+#include "snap_internal.h"
+
+#include <atomic>
+#include <functional>
+#include <vector>
+
+namespace snapk {
+
+struct HostAlloc {
+    void *ptr;
+    uint64_t bytes;
+};
+
+struct ImageHeader {
+    uint32_t flags;
+    uint64_t chunk_bytes, n_allocs, total, generation, parent;
+};
+
+// Everything one launch sequence needs that changes from call to call; the
+// host fills a pinned copy and the captured graph's first node copies it in.
+struct CallBlock {
+    unsigned long long cursor[4];  // tile cursors of the sequence's launches
+    Result res;
+    CallParams cp;
+    Job jobs[kMaxJobs];
+};
+
+enum EventId { EV_BEGIN = 0, EV_HASH_END, EV_DIFF_END, EV_COPY_END, EV_END, EV_COUNT };
+enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY };
+enum ShapeKind { SHAPE_GATHER = 0, SHAPE_HASH, SHAPE_SCATTER, SHAPE_COUNT };
+
+struct GraphEntry {
+    int kind;
+    int parity;
+    cudaGraphExec_t exec;
+};
+
+struct Ring;
+
+}  // namespace snapk
+
+struct snap_set_s {
+    int device = 0;
+    int sms = 148;
+    char gpu_name[128] = {0};
+    uint64_t C = 65536;
+    uint32_t timeout_ms = 10000;
+    cudaStream_t user_stream = nullptr;  // the caller's stream (quiesced)
+    cudaStream_t st = nullptr;           // library stream
+    snap_opts opts{};
+
+    std::vector<snapk::HostAlloc> allocs;
+    std::vector<snapk::AllocDesc> desc;
+    bool layout_dirty = true;
+    uint64_t n_chunks = 0, total_bytes = 0, full_bytes = 0, patch_bound = 0;
+
+    // device arrays (rebuilt with the layout)
+    snapk::AllocDesc *d_allocs = nullptr;
+    uint32_t *d_hash[2] = {nullptr, nullptr};  // committed table = d_hash[prev_idx]
+    uint32_t *d_cmp = nullptr;                 // verify: expected hashes
+    unsigned int *d_blockcnt = nullptr;
+    unsigned long long *d_blockoff = nullptr;
+    uint32_t *d_dlist = nullptr;
+    uint64_t *d_patch_rec = nullptr, *d_patch_data = nullptr, *d_dstart = nullptr;
+    uint32_t *h_hash_stage = nullptr;          // pinned, n_chunks hashes
+
+    // per-call block
+    snapk::CallBlock *d_cb = nullptr;
+    snapk::CallBlock *h_cb = nullptr;
+    snapk::Result *h_res = nullptr;
+
+    // committed state
+    int prev_idx = 0;
+    bool has_base = false;
+    uint64_t base_gen = 0;
+    uint64_t next_gen = 0;
+
+    std::vector<snapk::GraphEntry> graphs;
+    snapk::TileShape shape[snapk::SHAPE_COUNT];
+    std::atomic<bool> busy{false};
+    bool in_flight = false;
+    cudaEvent_t ev_quiesce = nullptr;
+    cudaEvent_t ev[snapk::EV_COUNT] = {};
+    snap_stats last{};
+
+    snapk::Ring *ring = nullptr;
+};
+
+namespace snapk {
+
+double now_ms();
+bool fault_injected(const char *what);
+int cuda_status(cudaError_t e);
+int wait_event(cudaEvent_t ev, double deadline_ms);
+uint8_t *mapped_device_ptr(const void *host);
+void write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n, uint64_t total, uint64_t gen, uint64_t parent);
+int parse_header(const uint8_t *img, uint64_t len, ImageHeader *h);
+int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes);
+int apply_patch_host(uint8_t *base, uint64_t base_len, const uint8_t *patch, uint64_t patch_len);
+
+// launch shapes (tune.cu)
+void default_shapes(snap_set_s *s);
+
+// pageable images through the pinned ring (ring.cu)
+int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
+                    double deadline);
+int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const ImageHeader &h, double t0, double tq,
+                 double deadline);
+void ring_free(snap_set_s *s);
+
+}  // namespace snapk

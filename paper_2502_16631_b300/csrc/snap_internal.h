@@ -88,6 +88,13 @@ struct CombineConsts {
     uint32_t pad[3];
 };
 
+// Per-call values read by the metadata kernels from device memory, so that
+// one captured graph serves every call (the host rewrites them per call).
+struct CallParams {
+    uint8_t *image;  // device-visible address of the host image
+    uint64_t cap;    // its capacity in bytes
+};
+
 size_t tile_smem_bytes(const TileShape &sh);
 constexpr size_t kMaxSmem = 232448;  // 227 KiB opt-in per CTA
 
@@ -98,17 +105,17 @@ cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cu
 CombineConsts make_combine_consts(uint64_t chunk_bytes, int piece);
 cudaError_t init_tile_kernel();
 cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
-                             uint8_t *image, cudaStream_t st);
+                             const CallParams *cp, cudaStream_t st);
 cudaError_t launch_diff(const uint32_t *cur, const uint32_t *prev, uint64_t n_chunks,
                         unsigned int *blockcnt, unsigned long long *blockoff, uint32_t *dlist,
                         Result *res, cudaStream_t st);
 cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
                                 const uint32_t *dlist, uint64_t *patch_rec, uint64_t *patch_data,
-                                uint64_t *dstart, uint64_t cap, Result *res, cudaStream_t st);
+                                uint64_t *dstart, const CallParams *cp, Result *res, cudaStream_t st);
 cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
                               const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
                               const uint64_t *patch_data, const uint64_t *dstart,
-                              const Result *res, uint8_t *image, cudaStream_t st);
+                              const Result *res, const CallParams *cp, cudaStream_t st);
 
 constexpr int kDiffBlock = 1024;
 

@@ -1,0 +1,164 @@
+// Launch shapes of the persistent tile kernel and the autotuner.
+//
+// The shape (warps per CTA, staging buffers per warp, bytes per lane per
+// stage, CTAs) decides how much data each SM keeps in flight and how much
+// shared memory the staging takes next to the 128 KiB of CRC tables.  The
+// autotuner times a set's own hash pass or full gather over a grid of
+// shapes that fit in shared memory, adopts the fastest, and appends it to a
+// cache file keyed by GPU name, operation, chunk size and state size class.
+#include "snap.h"
+#include "runtime_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+namespace snapk {
+
+static int ctas_per_sm(const snap_set_s *s) { return s->opts.ctas_per_sm ? (int)s->opts.ctas_per_sm : 1; }
+
+void default_shapes(snap_set_s *s)
+{
+    const int c = s->sms * ctas_per_sm(s);
+    s->shape[SHAPE_GATHER] = TileShape{4, 2, 256, c};
+    s->shape[SHAPE_HASH] = TileShape{10, 2, 128, c};
+    s->shape[SHAPE_SCATTER] = TileShape{16, 1, 64, c};
+    if (s->opts.stages)
+        for (int k = 0; k < SHAPE_COUNT; ++k) {
+            TileShape t = s->shape[k];
+            t.stages = (int)s->opts.stages;
+            if (tile_smem_bytes(t) <= kMaxSmem) s->shape[k] = t;
+        }
+}
+
+static int size_class(uint64_t bytes)
+{
+    int c = 0;
+    while (bytes > 1) {
+        bytes >>= 1;
+        ++c;
+    }
+    return c;
+}
+
+static std::string cache_path()
+{
+    const char *p = std::getenv("SNAP_TUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+static void cache_store(const snap_set_s *s, int mode, const TileShape &t, double gbs)
+{
+    const std::string p = cache_path();
+    if (p.empty()) return;
+    FILE *f = std::fopen(p.c_str(), "a");
+    if (!f) return;
+    std::fprintf(f, "{\"gpu\": \"%s\", \"op\": %d, \"chunk\": %llu, \"class\": %d, \"warps\": %d, \"stages\": %d, "
+                    "\"piece\": %d, \"ctas\": %d, \"gbs\": %.3f}\n",
+                 s->gpu_name, mode, (unsigned long long)s->C, size_class(s->total_bytes), t.warps, t.stages, t.piece,
+                 t.ctas, gbs);
+    std::fclose(f);
+}
+
+// Time one launch of a single-job tile kernel over the whole set.
+static int time_shape(snap_set_s *s, uint32_t op, uint8_t *dimg, const TileShape &t, double *ms)
+{
+    CallBlock &cb = *s->h_cb;
+    std::memset(&cb, 0, sizeof(CallBlock));
+    Job j{};
+    j.allocs = s->d_allocs;
+    j.n_allocs = s->desc.size();
+    j.chunk_bytes = s->C;
+    j.n_tiles = s->n_chunks;
+    j.op = op;
+    j.layout = LAYOUT_IMAGE;
+    j.host = dimg;
+    j.hash_out = s->d_cmp;  // scratch table: the committed one is untouched
+    j.res = &s->d_cb->res;
+    cb.jobs[0] = j;
+    const CombineConsts cc = make_combine_consts(s->C, t.piece);
+    cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, sizeof(CallBlock), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_BEGIN], s->st);
+    if (e == cudaSuccess) e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, t, &s->d_cb->res, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_END], s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->h_res->err) return SNAP_ECUDA;
+    float f = 0.f;
+    cudaEventElapsedTime(&f, s->ev[EV_BEGIN], s->ev[EV_END]);
+    *ms = f;
+    return SNAP_OK;
+}
+
+}  // namespace snapk
+
+using namespace snapk;
+
+extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap, snap_tuning *out)
+{
+    if (!s || (mode != SNAP_FULL && mode != SNAP_INCREMENTAL)) return SNAP_EINVAL;
+    uint64_t need = 0;
+    int rc = snap_image_bytes(s, SNAP_FULL, &need);
+    if (rc) return rc;
+    if (s->busy.exchange(true)) return SNAP_EBUSY;
+    struct Release {
+        snap_set_s *s;
+        ~Release() { s->busy.store(false); }
+    } rel{s};
+    cudaSetDevice(s->device);
+    if (s->in_flight) return SNAP_EBUSY;
+    uint8_t *dimg = nullptr;
+    if (mode == SNAP_FULL) {
+        if (!host_image || cap < need) return SNAP_EINVAL;
+        dimg = mapped_device_ptr(host_image);
+        if (!dimg) return SNAP_EINVAL;
+    }
+    if (s->n_chunks == 0) return SNAP_EINVAL;
+    const int kind = mode == SNAP_FULL ? SHAPE_GATHER : SHAPE_HASH;
+    const uint32_t op = mode == SNAP_FULL ? OP_GATHER : OP_HASH;
+    static const int warps_h[] = {6, 8, 10, 12, 16};
+    static const int warps_g[] = {2, 4, 8};
+    static const int stages_c[] = {2, 3, 4};
+    static const int piece_c[] = {64, 128, 256};
+    const int *wl = mode == SNAP_FULL ? warps_g : warps_h;
+    const int nw = mode == SNAP_FULL ? 3 : 5;
+    const int cps = s->opts.ctas_per_sm ? (int)s->opts.ctas_per_sm : 1;
+    TileShape best = s->shape[kind];
+    double best_ms = 1e30;
+    for (int a = 0; a < nw; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 3; ++c) {
+                TileShape t{wl[a], stages_c[b], piece_c[c], s->sms * cps};
+                if (tile_smem_bytes(t) > kMaxSmem) continue;
+                double ms = 0, m2 = 0;
+                rc = time_shape(s, op, dimg, t, &ms);  // warm
+                if (rc) return rc;
+                rc = time_shape(s, op, dimg, t, &m2);
+                if (rc) return rc;
+                ms = std::min(ms, m2);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+    s->shape[kind] = best;
+    if (mode == SNAP_INCREMENTAL) {
+        // verify runs the same hash pass
+    }
+    for (auto &g : s->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
+    const double gbs = (double)s->total_bytes / (best_ms * 1e-3) / 1e9;
+    cache_store(s, mode, best, gbs);
+    if (out) {
+        out->warps = (uint32_t)best.warps;
+        out->stages = (uint32_t)best.stages;
+        out->piece_bytes = (uint32_t)best.piece;
+        out->ctas_per_sm = (uint32_t)cps;
+        out->gbs = gbs;
+    }
+    return SNAP_OK;
+}

@@ -1,0 +1,357 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Everything here is integer/byte work, so the bar is bit-exact: every image
+byte, every hash and every restored byte equals what the oracle computes from
+the same device bytes (read back with a plain device-to-host copy, not
+through the library)."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_2502_16631_b300 as snap
+import workloads
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _oracle_threads():
+    oracle.set_threads(min(16, len(os.sched_getaffinity(0))))
+    yield
+    oracle.set_threads(1)
+
+
+def device_state(sizes, seed=1, offset=0):
+    """Device buffers with xorshift64* contents; returns (tensors, host copies).
+    offset (multiple of 16) shifts each buffer inside a larger allocation."""
+    ts, hs = [], []
+    for k, s in enumerate(sizes):
+        h = workloads.xorshift_bytes(s, seed, k)
+        base = torch.empty(s + offset + 16, dtype=torch.uint8, device="cuda")
+        t = base[offset: offset + s]
+        if s:
+            t.copy_(torch.from_numpy(h))
+        ts.append(t)
+        hs.append(h)
+    torch.cuda.synchronize()
+    return ts, hs
+
+
+def readback(ts):
+    torch.cuda.synchronize()
+    return [t.cpu().numpy().copy() if t.numel() else np.zeros(0, np.uint8) for t in ts]
+
+
+def make_set(ts, C=65536, **kw):
+    s = snap.Set(chunk_bytes=C, **kw)
+    for t in ts:
+        s.register(t.data_ptr() if t.numel() else 0, t.numel())
+    s.tensors = ts
+    return s
+
+
+# ------------------------------------------------------------ chunk hasher
+@pytest.mark.parametrize("C", [4096, 16384, 65536, 1 << 20])
+def test_hash_chunks_lengths(C):
+    rng = np.random.default_rng(C)
+    big = rng.integers(0, 256, 3 * C + 8192, dtype=np.uint8)
+    dbig = torch.from_numpy(big).cuda()
+    lengths = sorted(set([1, 2, 15, 16, 17, 31, 33, 100, 511, 513, 4095, 4096, 4097,
+                          C - 16, C - 1, C, C + 1, C + 15, 2 * C + 48, 3 * C + 8192]
+                         + list(rng.integers(1, 3 * C + 8192, 12))))
+    out = torch.zeros(8, dtype=torch.int32, device="cuda")
+    for n in lengths:
+        n = int(n)
+        nch = (n + C - 1) // C
+        out = torch.zeros(nch, dtype=torch.int32, device="cuda")
+        snap.hash_chunks(dbig, C, out, nbytes=n)
+        got = out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.chunk_hashes(big[:n], C)), (C, n)
+
+
+def test_hash_chunks_every_small_length():
+    rng = np.random.default_rng(5)
+    big = rng.integers(0, 256, 4096 + 600, dtype=np.uint8)
+    dbig = torch.from_numpy(big).cuda()
+    out = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for n in range(1, 600):
+        snap.hash_chunks(dbig, 4096, out, nbytes=n)
+        assert int(out[0].item()) & 0xFFFFFFFF == oracle.crc32c(big[:n]), n
+
+
+def test_hash_chunks_offsets_and_alignment():
+    rng = np.random.default_rng(6)
+    big = rng.integers(0, 256, 1 << 20, dtype=np.uint8)
+    dbig = torch.from_numpy(big).cuda()
+    out = torch.zeros(64, dtype=torch.int32, device="cuda")
+    for off in (16, 48, 4096 + 32, 65536 + 16):
+        n = (1 << 20) - off - 5
+        snap.hash_chunks(dbig.data_ptr() + off, 65536, out, nbytes=n)
+        exp = oracle.chunk_hashes(big[off: off + n], 65536)
+        assert np.array_equal(out[: exp.size].cpu().numpy().view(np.uint32), exp)
+    # a device pointer that is not 16-byte aligned is refused, not read
+    rc = snap.lib().snap_hash_chunks(dbig.data_ptr() + 3, 100, 65536, out.data_ptr(), None)
+    assert rc == snap.EINVAL
+
+
+def test_hash_chunks_check_value():
+    d = torch.tensor(list(b"123456789"), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    snap.hash_chunks(d, 4096, out)
+    assert int(out.item()) & 0xFFFFFFFF == 0xE3069283
+
+
+# ------------------------------------------------------ full image, restore
+SIZES_EDGE = [65536, 4096 * 3 + 16, 1, 0, 200000, 65536 * 2, 12345, 17, 65537, 3 * 65536 - 1]
+
+
+@pytest.mark.parametrize("C", [4096, 65536, 1 << 20])
+def test_full_checkpoint_matches_oracle(C):
+    ts, _ = device_state(SIZES_EDGE, seed=11)
+    s = make_set(ts, C)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    img.array[:] = 0xA5  # garbage: every padding byte must be written
+    used = s.checkpoint(img, snap.FULL)
+    rc, exp = oracle.write_full(readback(ts), C, generation=0)
+    assert rc == 0 and used == exp.size
+    assert np.array_equal(img.view(used), exp)
+    # second checkpoint: generation 1
+    used = s.checkpoint(img, snap.FULL)
+    rc, exp = oracle.write_full(readback(ts), C, generation=1)
+    assert np.array_equal(img.view(used), exp)
+
+
+def test_config1_roundtrip():
+    sizes = workloads.config1_sizes(1)
+    ts, hs = device_state(sizes, seed=1)
+    s = make_set(ts, 65536)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    rc, exp = oracle.write_full(hs, 65536, 0)
+    assert np.array_equal(img.view(used), exp)
+    for t in ts:
+        t.zero_()
+    s.restore(img, used)
+    for t, h in zip(readback(ts), hs):
+        assert np.array_equal(t, h)
+    assert s.verify(img, used) == 0
+    # committed hashes = image hashes, generation adopted
+    hh, gen = s.committed_hashes(sum((x + 65535) // 65536 for x in sizes))
+    assert gen == 0
+    assert np.array_equal(hh, np.concatenate([oracle.chunk_hashes(h, 65536) for h in hs]))
+
+
+def test_restore_into_fresh_buffers_and_verify_counts():
+    ts, hs = device_state(SIZES_EDGE, seed=12)
+    s = make_set(ts, 4096)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    fresh = [torch.zeros_like(t) for t in ts]
+    s2 = make_set(fresh, 4096)
+    s2.restore(img, used)
+    for a, b in zip(readback(fresh), hs):
+        assert np.array_equal(a, b)
+    # corrupt two chunks on the device: verify counts exactly those
+    fresh[4][5000] ^= 1
+    fresh[0][0] ^= 0x80
+    assert s2.verify(img, used) == 2
+
+
+def test_plain_form_data_regions():
+    ts, hs = device_state(SIZES_EDGE, seed=13)
+    s = make_set(ts, 65536)
+    n = s.image_bytes(snap.FULL)
+    img = snap.HostBuffer(n)
+    s.plain_checkpoint(img)
+    rc, exp = oracle.write_full(hs, 65536, 0)
+    # data regions equal the oracle's (headers/hashes are not written by the plain form)
+    off = 64
+    for h in hs:
+        nk = (h.size + 65535) // 65536
+        d = (off + 32 + 4 * nk + 4095) // 4096 * 4096
+        assert np.array_equal(img.array[d: d + h.size], h)
+        off = (d + h.size + 4095) // 4096 * 4096
+    for t in ts:
+        t.zero_()
+    s.plain_restore(img)
+    for a, b in zip(readback(ts), hs):
+        assert np.array_equal(a, b)
+
+
+# -------------------------------------------------------------- incremental
+def mutate(ts, C, chunks, seed=9):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for k, i in chunks:
+        lo, hi = i * C, min((i + 1) * C, ts[k].numel())
+        x = torch.randint(1, 256, (hi - lo,), dtype=torch.uint8, device="cuda", generator=g)
+        ts[k][lo:hi] ^= x
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("C", [4096, 65536])
+def test_incremental_patch_matches_oracle(C):
+    ts, _ = device_state(SIZES_EDGE, seed=14)
+    s = make_set(ts, C)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    patch.array[:] = 0x5A
+    used0 = s.checkpoint(full, snap.FULL)
+    base = readback(ts)
+    prev = [oracle.chunk_hashes(h, C) for h in base]
+    nch = [(x + C - 1) // C for x in SIZES_EDGE]
+    dirty = [(0, 0), (2, 0), (4, nch[4] - 1), (5, 1), (6, 0), (9, nch[9] - 1), (8, 1)]
+    mutate(ts, C, dirty)
+    used = s.checkpoint(patch, snap.INCREMENTAL)
+    cur = readback(ts)
+    rc, exp, nd = oracle.write_patch(cur, C, prev, generation=1, parent=0)
+    assert rc == 0 and nd == len(set(dirty))
+    assert used == exp.size
+    assert np.array_equal(patch.view(used), exp)
+    assert s.stats()["dirty_chunks"] == nd
+    # previous image + patch == full image of the current state
+    merged = full.view(used0).copy()
+    snap.apply_patch(merged, patch.view(used))
+    rc, full1 = oracle.write_full(cur, C, generation=1)
+    assert np.array_equal(merged, full1)
+    # a second incremental with nothing changed: headers and hashes only
+    used2 = s.checkpoint(patch, snap.INCREMENTAL)
+    rc, exp2, nd2 = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in cur], 2, 1)
+    assert nd2 == 0 and np.array_equal(patch.view(used2), exp2)
+
+
+def test_incremental_everything_dirty():
+    C = 4096
+    ts, _ = device_state([C * 5, C * 3 + 100, 77], seed=15)
+    s = make_set(ts, C)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    used0 = s.checkpoint(full, snap.FULL)
+    prev = [oracle.chunk_hashes(h, C) for h in readback(ts)]
+    mutate(ts, C, [(k, i) for k, t in enumerate(ts) for i in range((t.numel() + C - 1) // C)])
+    used = s.checkpoint(patch, snap.INCREMENTAL)
+    cur = readback(ts)
+    rc, exp, nd = oracle.write_patch(cur, C, prev, 1, 0)
+    assert np.array_equal(patch.view(used), exp)
+    merged = full.view(used0).copy()
+    snap.apply_patch(merged, patch.view(used))
+    assert np.array_equal(merged, oracle.write_full(cur, C, 1)[1])
+
+
+def test_incremental_errors_keep_base():
+    C = 4096
+    ts, _ = device_state([C * 8], seed=16)
+    s = make_set(ts, C)
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    rc, _ = s.checkpoint_status(patch, snap.INCREMENTAL)
+    assert rc == snap.ENOBASE
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    s.checkpoint(full, snap.FULL)
+    h0, g0 = s.committed_hashes(8)
+    mutate(ts, C, [(0, i) for i in range(8)])
+    # capacity too small for the patch: EINVAL, and nothing is committed
+    rc, _ = s.checkpoint_status(patch, snap.INCREMENTAL, cap=C * 2)
+    assert rc == snap.EINVAL
+    h1, g1 = s.committed_hashes(8)
+    assert np.array_equal(h0, h1) and g0 == g1
+    used = s.checkpoint(patch, snap.INCREMENTAL)
+    assert s.stats()["dirty_chunks"] == 8 and used > 8 * C
+
+
+# ----------------------------------------------------------------- errors
+def test_restore_rejects_mismatch_and_bad_images():
+    ts, _ = device_state([65536, 5000], seed=17)
+    s = make_set(ts, 65536)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    other, _ = device_state([65536, 5001], seed=17)
+    s2 = make_set(other, 65536)
+    assert s2.restore_status(img, used) == snap.EMISMATCH
+    s3 = make_set(other[:1], 65536)
+    assert s3.restore_status(img, used) == snap.EMISMATCH
+    s4 = make_set(ts, 4096)
+    assert s4.restore_status(img, used) == snap.EMISMATCH
+    img.array[3] ^= 1
+    assert s.restore_status(img, used) == snap.EFORMAT
+    img.array[3] ^= 1
+    assert s.restore_status(img, used - 4096) == snap.EFORMAT
+    assert s.restore_status(img, used) == snap.OK
+
+
+def test_register_rejects_misaligned_pointer():
+    t = torch.zeros(1024, dtype=torch.uint8, device="cuda")
+    s = snap.Set()
+    with pytest.raises(snap.SnapError):
+        s.register(t.data_ptr() + 4, 100)
+
+
+def test_quiesce_timeout_then_recovers():
+    """The lock waits for the caller's stream with a deadline (Sec. 3.1.1)."""
+    st = torch.cuda.Stream()
+    ts, hs = device_state([65536 * 4], seed=18)
+    s = make_set(ts, 65536, stream=st, timeout_ms=100)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    with torch.cuda.stream(st):
+        torch.cuda._sleep(int(2e9))  # about a second of queued work on the caller's stream
+    rc, _ = s.checkpoint_status(img, snap.FULL)
+    assert rc == snap.ETIMEDOUT
+    with pytest.raises(snap.SnapError):
+        s.committed_hashes(4)  # nothing was committed
+    st.synchronize()
+    used = s.checkpoint(img, snap.FULL)
+    assert np.array_equal(img.view(used), oracle.write_full(hs, 65536, 0)[1])
+
+
+def test_injected_allocation_failure_leaves_set_usable(monkeypatch):
+    ts, hs = device_state([70000], seed=19)
+    s = make_set(ts, 4096)
+    monkeypatch.setenv("SNAP_FAULT", "hash_alloc")
+    with pytest.raises(snap.SnapError) as e:
+        s.image_bytes(snap.FULL)
+    assert e.value.status == snap.ENOMEM
+    monkeypatch.delenv("SNAP_FAULT")
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    assert np.array_equal(img.view(used), oracle.write_full(hs, 4096, 0)[1])
+
+
+def test_injected_graph_failure(monkeypatch):
+    ts, hs = device_state([70000], seed=20)
+    s = make_set(ts, 4096)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    monkeypatch.setenv("SNAP_FAULT", "graph")
+    rc, _ = s.checkpoint_status(img, snap.FULL)
+    assert rc == snap.ENOMEM
+    monkeypatch.delenv("SNAP_FAULT")
+    used = s.checkpoint(img, snap.FULL)
+    assert np.array_equal(img.view(used), oracle.write_full(hs, 4096, 0)[1])
+
+
+# ------------------------------------------------------------ config 2 size
+def test_gpt2_state_full_parity():
+    """GPT-2-small training state (593 allocations, 2,259,472,384 B): the
+    batched persistent kernel's image equals the oracle's, byte for byte."""
+    spec = workloads.gpt2_state_spec()
+    sizes = workloads.spec_bytes(spec)
+    ts = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+    workloads.torch_fill_spec(ts, spec, seed=2)
+    s = make_set(ts, 65536)
+    n = s.image_bytes(snap.FULL)
+    img = snap.HostBuffer(n)
+    used = s.checkpoint(img, snap.FULL)
+    host = readback(ts)
+    rc, exp = oracle.write_full(host, 65536, 0)
+    assert rc == 0 and np.array_equal(img.view(used), exp)
+    del exp
+    for t in ts:
+        t.zero_()
+    s.restore(img, used)
+    for a, b in zip(readback(ts), host):
+        assert np.array_equal(a, b)
