@@ -96,6 +96,7 @@ typedef struct {
     double diff_ms;          /* dirty diff + compaction + patch layout    */
     double copy_ms;          /* gather (checkpoint) or scatter (restore)  */
     double total_ms;         /* call entry to return                      */
+    uint64_t kernel_launches; /* libsnap kernels the call ran on the GPU  */
 } snap_stats;
 
 /* ------------------------------------------------------------------ sets */

@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
                 ("mismatches", ctypes.c_uint64), ("generation", ctypes.c_uint64),
                 ("quiesce_ms", ctypes.c_double), ("hash_ms", ctypes.c_double),
                 ("diff_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -11,6 +11,19 @@ namespace snapk {
 
 __device__ __forceinline__ uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
 
+__global__ void k_stamp(Result *res, int idx)
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    res->ts[idx] = t;
+}
+
+cudaError_t launch_stamp(Result *res, int idx, cudaStream_t st)
+{
+    k_stamp<<<1, 1, 0, st>>>(res, idx);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------ full image: record headers
 // Block k writes allocation k's 32-byte record {bytes, n, data_off, 0} and
 // zeroes the padding between its hash array and its data.  (The hashes, the

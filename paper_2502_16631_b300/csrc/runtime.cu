@@ -290,13 +290,24 @@ static int run_graph(snap_set_s *s, int kind, int parity, const std::function<cu
             if (graph) cudaGraphDestroy(graph);
             return cuda_status(eb != cudaSuccess ? eb : e);
         }
+        uint64_t kernels = 0;
+        size_t nn = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                for (auto n : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(n, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kernels;
+                }
+        }
         cudaGraphExec_t exec = nullptr;
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_status(e);
-        s->graphs.push_back(GraphEntry{kind, parity, exec});
+        s->graphs.push_back(GraphEntry{kind, parity, exec, kernels});
         g = &s->graphs.back();
     }
+    s->call_kernels = g->kernels;
     return cuda_status(cudaGraphLaunch(g->exec, s->st));
 }
 
@@ -328,14 +339,21 @@ static Job base_job(const snap_set_s *s, uint32_t op)
 static cudaError_t enqueue_prologue(snap_set_s *s, cudaStream_t st)
 {
     cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, sizeof(CallBlock), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_BEGIN], st);
+    if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_BEGIN, st);
     return e;
 }
 static cudaError_t enqueue_epilogue(snap_set_s *s, cudaStream_t st)
 {
-    cudaError_t e = cudaEventRecord(s->ev[EV_COPY_END], st);
+    cudaError_t e = launch_stamp(&s->d_cb->res, TS_COPY_END, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, st);
     return e;
+}
+
+// Milliseconds between two device stamps of the last launch sequence.
+static double ts_ms(const snap_set_s *s, int a, int b)
+{
+    const unsigned long long ta = s->h_res->ts[a], tb = s->h_res->ts[b];
+    return (ta && tb && tb >= ta) ? (double)(tb - ta) * 1e-6 : 0.0;
 }
 
 static float ev_ms(snap_set_s *s, int a, int b)
@@ -551,7 +569,7 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
                      s->total_bytes, gen, 0);
         *used = s->full_bytes;
         st.image_bytes = s->full_bytes;
-        st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+        st.copy_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
         st.dirty_chunks = s->n_chunks;
     } else {
         Job jh = base_job(s, OP_HASH);
@@ -574,7 +592,7 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
             cudaError_t e = enqueue_prologue(s, q);
             if (e == cudaSuccess && s->n_chunks)
                 e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cch, shh, &s->d_cb->res, q);
-            if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_HASH_END], q);
+            if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_HASH_END, q);
             if (e == cudaSuccess)
                 e = launch_diff(curp, prevp, s->n_chunks, s->d_blockcnt, s->d_blockoff, s->d_dlist, &s->d_cb->res, q);
             if (e == cudaSuccess)
@@ -583,7 +601,7 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
             if (e == cudaSuccess)
                 e = launch_patch_meta(s->d_allocs, s->desc.size(), s->C, curp, s->d_dlist, s->d_patch_rec,
                                       s->d_patch_data, s->d_dstart, &s->d_cb->res, &s->d_cb->cp, q);
-            if (e == cudaSuccess) e = cudaEventRecord(s->ev[EV_DIFF_END], q);
+            if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_DIFF_END, q);
             if (e == cudaSuccess && s->n_chunks)
                 e = launch_tiles(s->d_cb->jobs + 1, 1, &s->d_cb->cursor[1], ccg, shg, &s->d_cb->res, q);
             if (e == cudaSuccess) e = enqueue_epilogue(s, q);
@@ -597,9 +615,9 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
         *used = s->h_res->patch_bytes;
         st.image_bytes = s->h_res->patch_bytes;
         st.dirty_chunks = s->h_res->n_dirty;
-        st.hash_ms = ev_ms(s, EV_BEGIN, EV_HASH_END);
-        st.diff_ms = ev_ms(s, EV_HASH_END, EV_DIFF_END);
-        st.copy_ms = ev_ms(s, EV_DIFF_END, EV_COPY_END);
+        st.hash_ms = ts_ms(s, TS_BEGIN, TS_HASH_END);
+        st.diff_ms = ts_ms(s, TS_HASH_END, TS_DIFF_END);
+        st.copy_ms = ts_ms(s, TS_DIFF_END, TS_COPY_END);
     }
     // commit (Sec. 3.1: only a completed checkpoint replaces the base)
     s->prev_idx = cur;
@@ -610,6 +628,7 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
     st.total_chunks = s->n_chunks;
     st.generation = gen;
     st.quiesce_ms = tq - t0;
+    st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
     s->last = st;
     return SNAP_OK;
@@ -670,7 +689,8 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
     st.total_chunks = s->n_chunks;
     st.generation = h.generation;
     st.quiesce_ms = tq - t0;
-    st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.copy_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
+    st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
     s->last = st;
     return SNAP_OK;
@@ -721,7 +741,8 @@ int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_
     st.mismatches = s->h_res->mismatches;
     st.generation = h.generation;
     st.quiesce_ms = tq - t0;
-    st.hash_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
+    st.hash_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
+    st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
     s->last = st;
     return SNAP_OK;

@@ -36,6 +36,7 @@ struct GraphEntry {
     int kind;
     int parity;
     cudaGraphExec_t exec;
+    uint64_t kernels;  // kernel nodes in the graph
 };
 
 struct Ring;
@@ -85,6 +86,7 @@ struct snap_set_s {
     cudaEvent_t ev_quiesce = nullptr;
     cudaEvent_t ev[snapk::EV_COUNT] = {};
     snap_stats last{};
+    uint64_t call_kernels = 0;  // kernels launched by the current call
 
     snapk::Ring *ring = nullptr;
 };

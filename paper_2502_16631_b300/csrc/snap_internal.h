@@ -41,7 +41,10 @@ struct Result {
     unsigned long long patch_bytes;  // incremental: patch size
     unsigned long long cap_exceeded; // incremental: patch larger than the image capacity
     unsigned long long pad[2];
+    unsigned long long ts[8];        // %globaltimer stamps between the phases (ns)
 };
+
+enum StampId { TS_BEGIN = 0, TS_HASH_END, TS_DIFF_END, TS_COPY_END };
 
 enum ResultErr : unsigned long long {
     ERR_WAIT_TIMEOUT = 1ull,   // an mbarrier wait passed its deadline
@@ -116,6 +119,10 @@ cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64
                               const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
                               const uint64_t *patch_data, const uint64_t *dstart,
                               const Result *res, const CallParams *cp, cudaStream_t st);
+
+// One-thread kernel recording the device clock into res->ts[idx]; stream
+// order makes it a phase boundary inside a captured graph.
+cudaError_t launch_stamp(Result *res, int idx, cudaStream_t st);
 
 constexpr int kDiffBlock = 1024;
 
