@@ -1,0 +1,48 @@
+"""Small, fixed workloads for ncu captures of single kernels (run by hand
+under `ncu`; not collected by pytest).
+
+    python tests/profile_cases.py gather [reps]   # 8 x 64 MiB, full checkpoints
+    python tests/profile_cases.py scatter [reps]  # 8 x 64 MiB, restores
+    python tests/profile_cases.py hash [reps]     # 1 GiB chunk hasher
+"""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import torch  # noqa: E402
+
+import paper_2502_16631_b300 as snap  # noqa: E402
+
+MiB = 1 << 20
+
+
+def main():
+    op = sys.argv[1]
+    reps = int(sys.argv[2]) if len(sys.argv) > 2 else 2
+    if op == "hash":
+        x = torch.empty(1024 * MiB, dtype=torch.uint8, device="cuda")
+        x.random_(0, 256)
+        h = torch.empty(1024 * MiB // 65536, dtype=torch.int32, device="cuda")
+        for _ in range(reps):
+            snap.hash_chunks(x, 65536, h)
+    else:
+        ts = [torch.empty(64 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]
+        for t in ts:
+            t.random_(0, 256)
+        s = snap.Set(chunk_bytes=65536)
+        for t in ts:
+            s.register(t)
+        img = snap.HostBuffer(s.image_bytes(snap.FULL))
+        used = s.checkpoint(img, snap.FULL)
+        for _ in range(reps):
+            if op == "gather":
+                s.checkpoint(img, snap.FULL)
+            else:
+                s.restore(img, used)
+    torch.cuda.synchronize()
+    print("done", op)
+
+
+if __name__ == "__main__":
+    main()
