@@ -191,6 +191,26 @@ SNAP_API int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set
 SNAP_API int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_bytes,
                      uint32_t *hashes, void *stream);
 
+/* Allocation-free chunk hasher (the paper has no counterpart: this serves
+ * callers that cannot allocate GPU memory -- a checkpoint or crash handler
+ * that must not touch the allocator whose state it is saving, a process
+ * whose memory pool is exhausted or owned by another framework).  Hashes
+ * n_buffers device buffers (each 16-byte aligned) in one launch: hashes (a
+ * device array) receives the chunk hashes of buffer 0, then buffer 1, ...,
+ * ceil(bytes[k]/chunk_bytes) entries each, as snap_hash_chunks would
+ * produce buffer by buffer.  It calls no cudaMalloc/cudaFree/cudaHostAlloc:
+ * its scratch is a fixed device array inside libsnap that every GPU using
+ * the library keeps until the process exits.  Limits: n_buffers <=
+ * SNAP_NOALLOC_MAX_BUFFERS, else SNAP_EINVAL with nothing launched.  The
+ * first call on each device looks up that array (cudaGetSymbolAddress):
+ * make it before any stream capture.  Calls share the array: two calls
+ * whose GPU work overlaps (other streams or threads on the same device)
+ * race; this process's host calls are serialised.  Runs on `stream` and
+ * waits for it. */
+#define SNAP_NOALLOC_MAX_BUFFERS 1024u
+SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *bytes, uint32_t n_buffers,
+                                      uint64_t chunk_bytes, uint32_t *hashes, void *stream);
+
 /* ----------------------------------------------------------- autotuning */
 typedef struct {
     uint32_t warps;        /* warps per CTA of the persistent kernel */

@@ -34,7 +34,8 @@ EXPORTS = (
     "snap_set_create", "snap_set_destroy", "snap_register", "snap_image_bytes",
     "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_restore", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
-    "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_autotune",
+    "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
+    "snap_autotune",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
 
@@ -100,6 +101,7 @@ def _lib():
             "snap_plain_checkpoint": [vp, vp, u64],
             "snap_plain_restore": [vp, u64, vp],
             "snap_hash_chunks": [vp, u64, u64, vp, vp],
+            "snap_hash_chunks_noalloc": [P(vp), P(u64), u32, u64, vp, vp],
             "snap_autotune": [vp, i32, vp, u64, P(Tuning)],
             "snap_server_create": [P(vp), u64, u64, P(Opts)],
             "snap_server_destroy": [vp],
@@ -279,6 +281,25 @@ def hash_chunks(dev_tensor, chunk_bytes: int, out, nbytes: int | None = None, st
     n = _nbytes(dev_tensor) if nbytes is None else nbytes
     _check(_lib().snap_hash_chunks(_addr(dev_tensor), n, chunk_bytes, _addr(out), _stream_handle(stream)),
            "snap_hash_chunks")
+
+
+NOALLOC_MAX_BUFFERS = 1024
+
+
+def hash_chunks_noalloc(buffers, chunk_bytes: int, out, stream=None) -> int:
+    """Chunk hashes of several device buffers (tensors, or (address, nbytes)
+    pairs) into the device array `out`, buffer after buffer, without any
+    GPU memory allocation (for callers that cannot allocate).  Returns the
+    status (0 on success)."""
+    n = len(buffers)
+    ptrs = (ctypes.c_void_p * max(1, n))()
+    sizes = (ctypes.c_uint64 * max(1, n))()
+    for k, b in enumerate(buffers):
+        if isinstance(b, tuple):
+            ptrs[k], sizes[k] = b[0], b[1]
+        else:
+            ptrs[k], sizes[k] = _addr(b), _nbytes(b)
+    return _lib().snap_hash_chunks_noalloc(ptrs, sizes, n, chunk_bytes, _addr(out), _stream_handle(stream))
 
 
 def _stream_handle(stream):
