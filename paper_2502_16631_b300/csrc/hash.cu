@@ -87,7 +87,7 @@ extern "C" int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk
     h.job.op = OP_HASH;
     h.job.hash_out = hashes;
     h.job.res = &c.d->res;
-    const TileShape sh{10, 2, 128, c.sms};
+    const TileShape sh = default_hash_shape(c.sms);
     const CombineConsts cc = make_combine_consts(chunk_bytes, sh.piece);
     cudaError_t e = cudaMemcpyAsync(c.d, c.h, sizeof(HashScratch), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_tiles(&c.d->job, 1, &c.d->cursor, cc, sh, &c.d->res, st);

@@ -36,7 +36,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 size_t tile_smem_bytes(const TileShape &sh)
 {
-    return kTableBytes + (size_t)sh.warps * sh.stages * 32 * (sh.piece + 16) +
+    return kTableBytes + (size_t)sh.warps * sh.stages * 32 * sh.chains * (sh.piece + 16) +
            (size_t)sh.warps * sh.stages * 8 + (kMaxJobs + 1) * 8;
 }
 
@@ -118,24 +118,47 @@ __device__ __forceinline__ void fence_mbar_init()
 }
 
 // ------------------------------------------------------------- CRC pieces
-// tl points at this lane's column of the replicated tables: entry (t, v) of
-// slicing table t is tl[(t * 256 + v) * 32], always in bank == lane.
-__device__ __forceinline__ uint32_t crc_word(uint32_t crc, uint32_t w, const uint32_t *tl)
+// Table layout (128 KiB): tables t = 2p + h (p = pair 0/1, h = half 0/1);
+// entry (t, v) of lane l is the 32-bit word at byte offset
+//     p * 65536 + v * 256 + h * 128 + l * 4,
+// i.e. each 256-byte row holds one value of two tables for all 32 lanes, so
+// a lane always reads its own bank, and the row offset v * 256 is a single
+// byte-permute of the CRC register.  `lb` is the lane's 32-bit shared
+// address of entry (0, 0); the pair/half part is an immediate offset.
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_tab(uint32_t addr)
+{
+    uint32_t v;
+    asm("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+__device__ __forceinline__ uint32_t crc_word(uint32_t crc, uint32_t w, uint32_t lb)
 {
     const uint32_t x = crc ^ w;
-    return tl[(768u + (x & 0xFFu)) << 5] ^ tl[(512u + ((x >> 8) & 0xFFu)) << 5] ^
-           tl[(256u + ((x >> 16) & 0xFFu)) << 5] ^ tl[(x >> 24) << 5];
+    // byte i of x, shifted to bits 8..15 (the row offset), others zero
+    const uint32_t a3 = lds_tab<65536 + 128>(lb + __byte_perm(x, 0u, 0x4404u));  // byte 0 -> table 3
+    const uint32_t a2 = lds_tab<65536>(lb + __byte_perm(x, 0u, 0x4414u));        // byte 1 -> table 2
+    const uint32_t a1 = lds_tab<128>(lb + __byte_perm(x, 0u, 0x4424u));          // byte 2 -> table 1
+    const uint32_t a0 = lds_tab<0>(lb + __byte_perm(x, 0u, 0x4434u));            // byte 3 -> table 0
+    return a0 ^ a1 ^ a2 ^ a3;
 }
-__device__ __forceinline__ uint32_t crc_byte(uint32_t crc, uint32_t b, const uint32_t *tl)
+__device__ __forceinline__ uint32_t crc_byte(uint32_t crc, uint32_t b, uint32_t lb)
 {
-    return tl[((crc ^ b) & 0xFFu) << 5] ^ (crc >> 8);
+    return lds_tab<0>(lb + (((crc ^ b) & 0xFFu) << 8)) ^ (crc >> 8);
 }
-__device__ __forceinline__ uint32_t crc_block(uint32_t crc, const uint4 v, const uint32_t *tl)
+__device__ __forceinline__ uint32_t crc_block(uint32_t crc, const uint4 v, uint32_t lb)
 {
-    crc = crc_word(crc, v.x, tl);
-    crc = crc_word(crc, v.y, tl);
-    crc = crc_word(crc, v.z, tl);
-    return crc_word(crc, v.w, tl);
+    crc = crc_word(crc, v.x, lb);
+    crc = crc_word(crc, v.y, lb);
+    crc = crc_word(crc, v.z, lb);
+    return crc_word(crc, v.w, lb);
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
 }
 __device__ __forceinline__ uint32_t warp_xor(uint32_t v)
 {
@@ -166,9 +189,9 @@ struct WarpCtx {
     uint32_t mbar;         // shared address of its first mbarrier
     uint32_t issued;       // stages issued so far (per warp, across chunks)
     uint32_t consumed;     // stages consumed so far
-    int stages, piece, lane;
-    const uint32_t *tl;    // lane column of the CRC tables
-    uint32_t stage_bytes;  // 32 * (piece + 16)
+    int stages, piece, lane, chains;
+    uint32_t lb;           // shared address of this lane's table column
+    uint32_t stage_bytes;  // 32 * chains * (piece + 16)
 };
 
 __device__ __forceinline__ uint32_t buf_of(const WarpCtx &w, uint32_t g) { return g % (uint32_t)w.stages; }
@@ -206,10 +229,118 @@ __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32
     cp_async_arrive(w.mbar + 8 * buf_of(w, g));
 }
 
+// Full chunk (L == C, C/32 a multiple of P): the copy plan of every stage is
+// the same up to a k*P offset, so each lane keeps one source and one
+// destination base; the CRC loop over the piece is fully unrolled.
+template <int P>
+__device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, const CombineConsts &cc, uint32_t &out)
+{
+    constexpr uint32_t BPP = P / 16;    // 16-byte blocks per piece
+    constexpr uint32_t PPI = 32 / BPP;  // pieces covered by one warp instruction
+    const uint32_t lane = (uint32_t)w.lane;
+    const uint32_t s = C >> 5;
+    const uint32_t nst = s / P;
+    const uint32_t jl = lane / BPP, bl = lane % BPP;
+    const uint8_t *sp0 = src + jl * s + 16u * bl;
+    const uint32_t d0 = jl * (P + 16u) + 16u * bl;
+    const uint32_t stage0 = smem_addr(w.stage);
+    const uint32_t S = (uint32_t)w.stages;
+    uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
+
+    auto issue = [&](uint32_t k) {
+        const uint32_t g = w.issued++;
+        const uint32_t sbs = stage0 + buf_of(w, g) * w.stage_bytes;
+#pragma unroll
+        for (uint32_t m = 0; m < BPP; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
+        cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+    };
+    const uint32_t pre = nst < S ? nst : S;
+    for (uint32_t k = 0; k < pre; ++k) issue(k);
+    for (uint32_t k = 0; k < nst; ++k) {
+        const uint32_t g = w.consumed;
+        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
+        w.consumed++;
+        const uint32_t rd = stage0 + buf_of(w, g) * w.stage_bytes + lane * (P + 16u);
+#pragma unroll
+        for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * b), w.lb);
+        __syncwarp();
+        if (k + S < nst) issue(k + S);
+    }
+    out = warp_xor(gf2_mulmod(crc, cc.kseg[lane])) ^ 0xFFFFFFFFu;
+    return true;
+}
+
+// Full chunk with two independent CRC chains per lane: the chunk is cut
+// into 64 segments of C/64 bytes; lane l hashes segments l and l+32, so
+// every lane has two lookup chains in flight.  A stage holds the next P
+// bytes of all 64 segments (slot v at v*(P+16), conflict-free reads).
+template <int P>
+__device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, const CombineConsts &cc, uint32_t &out)
+{
+    constexpr uint32_t BPP = P / 16;    // 16-byte blocks per piece
+    constexpr uint32_t PPI = 32 / BPP;  // pieces covered by one warp instruction
+    constexpr uint32_t NI = 64 / PPI;   // copy instructions per stage
+    const uint32_t lane = (uint32_t)w.lane;
+    const uint32_t s = C >> 6;
+    const uint32_t nst = s / P;
+    const uint32_t jl = lane / BPP, bl = lane % BPP;
+    const uint8_t *sp0 = src + jl * s + 16u * bl;
+    const uint32_t d0 = jl * (P + 16u) + 16u * bl;
+    const uint32_t stage0 = smem_addr(w.stage);
+    const uint32_t S = (uint32_t)w.stages;
+    uint32_t ca = lane == 0 ? 0xFFFFFFFFu : 0u, cb = 0u;
+
+    auto issue = [&](uint32_t k) {
+        const uint32_t g = w.issued++;
+        const uint32_t sbs = stage0 + buf_of(w, g) * w.stage_bytes;
+#pragma unroll
+        for (uint32_t m = 0; m < NI; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
+        cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+    };
+    const uint32_t pre = nst < S ? nst : S;
+    for (uint32_t k = 0; k < pre; ++k) issue(k);
+    for (uint32_t k = 0; k < nst; ++k) {
+        const uint32_t g = w.consumed;
+        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
+        w.consumed++;
+        const uint32_t ra = stage0 + buf_of(w, g) * w.stage_bytes + lane * (P + 16u);
+        const uint32_t rb = ra + 32u * (P + 16u);
+#pragma unroll
+        for (uint32_t b = 0; b < BPP; ++b) {
+            const uint4 va = lds128(ra + 16u * b);
+            const uint4 vb = lds128(rb + 16u * b);
+            ca = crc_block(ca, va, w.lb);
+            cb = crc_block(cb, vb, w.lb);
+        }
+        __syncwarp();
+        if (k + S < nst) issue(k + S);
+    }
+    const uint32_t v = gf2_mulmod(ca, cc.kseg2[lane]) ^ gf2_mulmod(cb, cc.kseg2[lane + 32]);
+    out = warp_xor(v) ^ 0xFFFFFFFFu;
+    return true;
+}
+
 // The chunk's CRC-32C lands in `out` in every lane; false if a wait gave up.
 __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t C, const CombineConsts &cc,
                                uint32_t &out)
 {
+    if (w.chains == 2 && L == C && ((C >> 6) % (uint32_t)w.piece) == 0u) {
+        switch (w.piece) {
+        case 32: return hash_full_chunk2<32>(w, src, C, cc, out);
+        case 64: return hash_full_chunk2<64>(w, src, C, cc, out);
+        case 128: return hash_full_chunk2<128>(w, src, C, cc, out);
+        default: break;
+        }
+    }
+    if (L == C && ((C >> 5) % (uint32_t)w.piece) == 0u) {
+        switch (w.piece) {
+        case 32: return hash_full_chunk<32>(w, src, C, cc, out);
+        case 64: return hash_full_chunk<64>(w, src, C, cc, out);
+        case 128: return hash_full_chunk<128>(w, src, C, cc, out);
+        case 256: return hash_full_chunk<256>(w, src, C, cc, out);
+        default: break;
+        }
+    }
     const int lane = w.lane;
     const uint32_t P = (uint32_t)w.piece;
     const uint32_t s = (L == C) ? (C >> 5) : ((((L + 31u) >> 5) + 15u) & ~15u);
@@ -234,14 +365,14 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
             const uint32_t nfull = (phi - plo) >> 4;
             if (nfull == (P >> 4)) {
 #pragma unroll 4
-                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.tl);
+                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.lb);
             } else {
-                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.tl);
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.lb);
             }
             const uint32_t rem = (phi - plo) & 15u;
             if (rem) {
                 const uint8_t *tp = src + plo + (nfull << 4);
-                for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.tl);
+                for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.lb);
             }
         }
         __syncwarp();
@@ -308,11 +439,11 @@ __device__ bool gather_chunk_int(WarpCtx &w, const uint8_t *src, uint32_t L, uin
                 if (crc != 0u && gap != 0u) crc = gf2_mulmod(crc, gap == 31u * P ? cc.kgap : gf2_x8n(gap, c_pow8));
                 const uint4 *sp = reinterpret_cast<const uint4 *>(sb + (uint32_t)lane * P);
                 const uint32_t nfull = (phi - plo) >> 4;
-                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.tl);
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.lb);
                 const uint32_t rem = (phi - plo) & 15u;
                 if (rem) {
                     const uint8_t *tp = src + plo + (nfull << 4);
-                    for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.tl);
+                    for (uint32_t r = 0; r < rem; ++r) crc = crc_byte(crc, __ldg(tp + r), w.lb);
                 }
                 e = phi;
             }
@@ -376,14 +507,14 @@ __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, u
 
 __global__ void __launch_bounds__(kMaxWarps * 32, 1)
 snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor, const CombineConsts cc,
-           int stages, int piece, Result *kres)
+           int stages, int piece, int chains, Result *kres)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint32_t *tables = reinterpret_cast<uint32_t *>(smem);
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t stage_bytes = 32u * (uint32_t)(piece + 16);
+    const uint32_t stage_bytes = 32u * (uint32_t)chains * (uint32_t)(piece + 16);
     uint8_t *stage_all = smem + kTableBytes;
     uint64_t *mbars = reinterpret_cast<uint64_t *>(stage_all + (size_t)warps * stages * stage_bytes);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(mbars + warps * stages);
@@ -393,8 +524,9 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
         need_tables |= (jobs[j].op == OP_HASH || jobs[j].op == OP_GATHER || jobs[j].op == OP_VERIFY);
     if (need_tables)
         for (int i = threadIdx.x; i < 32768; i += blockDim.x) {
-            const int tv = i >> 5;
-            tables[i] = g_slice.t[tv >> 8][tv & 255];
+            // word i: pair i>>14, row (i>>6)&255, half (i>>5)&1, lane i&31
+            const int t = ((i >> 14) << 1) | ((i >> 5) & 1);
+            tables[i] = g_slice.t[t][(i >> 6) & 255];
         }
     if (lane == 0)
         for (int s = 0; s < stages; ++s) mbar_init(smem_addr(&mbars[warp * stages + s]), 32);
@@ -416,8 +548,9 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
     w.issued = w.consumed = 0;
     w.stages = stages;
     w.piece = piece;
+    w.chains = chains;
     w.lane = lane;
-    w.tl = tables + lane;
+    w.lb = smem_addr(tables) + 4u * (uint32_t)lane;
     w.stage_bytes = stage_bytes;
 
     for (;;) {
@@ -501,7 +634,10 @@ cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cu
     const size_t smem = tile_smem_bytes(sh);
     if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxWarps || n_jobs < 1 || n_jobs > kMaxJobs)
         return cudaErrorInvalidValue;
-    snap_tiles<<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece, kres);
+    if (sh.chains < 1 || sh.chains > 2 || sh.stages < 1 || sh.piece < 32 || sh.piece > 256 || (sh.piece & 15))
+        return cudaErrorInvalidValue;
+    snap_tiles<<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece, sh.chains,
+                                                     kres);
     return cudaGetLastError();
 }
 
@@ -522,6 +658,7 @@ CombineConsts make_combine_consts(uint64_t C, int piece)
         cc.kseg[l] = gf2_x8n(C - (uint64_t)(l + 1) * s, pw);
         cc.kint[l] = gf2_x8n((uint64_t)(31 - l) * P, pw);
     }
+    for (int v = 0; v < 64; ++v) cc.kseg2[v] = gf2_x8n(C - (uint64_t)(v + 1) * (C / 64), pw);
     cc.kgap = gf2_x8n(31 * P, pw);
     return cc;
 }

@@ -131,7 +131,7 @@ extern "C" int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t
     h.job.res = &d->res;
     const size_t used = offsetof(NoAllocScratch, desc) + n_desc * sizeof(AllocDesc);
 
-    const TileShape sh{10, 2, 128, g_setup[dev].sms};
+    const TileShape sh = default_hash_shape(g_setup[dev].sms);
     const CombineConsts cc = make_combine_consts(chunk_bytes, sh.piece);
     // pageable source: the call returns once the bytes are staged, so the
     // static host block may be reused by the next call

@@ -105,6 +105,7 @@ int apply_patch_host(uint8_t *base, uint64_t base_len, const uint8_t *patch, uin
 
 // launch shapes (tune.cu)
 void default_shapes(snap_set_s *s);
+TileShape default_hash_shape(int ctas);
 
 // pageable images through the pinned ring (ring.cu)
 int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint64_t *used, double t0, double tq,

@@ -79,13 +79,15 @@ constexpr int kMaxWarps = 16;
 struct TileShape {
     int warps;        // warps per CTA
     int stages;       // staging buffers per warp
-    int piece;        // bytes per lane per stage: 64, 128 or 256
+    int piece;        // bytes per segment per stage: 32, 64, 128 or 256
     int ctas;         // grid size (persistent CTAs)
+    int chains = 1;   // hashing: independent CRC chains per lane (1 or 2)
 };
 
 // Combine constants, computed on the host for a chunk size and piece size.
 struct CombineConsts {
     uint32_t kseg[32];    // x^(8*(C - (l+1)*C/32)): segmented lane l of a full chunk
+    uint32_t kseg2[64];   // x^(8*(C - (v+1)*C/64)): segment v of 64 (two chains per lane)
     uint32_t kint[32];    // x^(8*(31-l)*P): interleaved lane l, end of a full chunk
     uint32_t kgap;        // x^(8*31*P): interleaved gap between a lane's pieces
     uint32_t pad[3];

@@ -265,6 +265,43 @@ def test_incremental_errors_keep_base():
     assert s.stats()["dirty_chunks"] == 8 and used > 8 * C
 
 
+# ------------------------------------------------------------- autotuner
+@pytest.mark.parametrize("C", [4096, 65536])
+def test_autotune_every_shape_agrees_then_parity(C):
+    """The autotuner runs every launch shape (warps, stages, piece bytes,
+    one or two CRC chains per lane) and fails if any two disagree on a
+    single chunk hash; the adopted shape must still match the oracle."""
+    sizes = [8 * C, 3 * C + 4096 + 16, 100000, 12345, C]
+    ts, hs = device_state(sizes, seed=31)
+    s = make_set(ts, C)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    t_inc = s.autotune(snap.INCREMENTAL)
+    t_full = s.autotune(snap.FULL, img)
+    assert t_inc["gbs"] > 0 and t_full["gbs"] > 0
+    used = s.checkpoint(img, snap.FULL)
+    assert np.array_equal(img.view(used), oracle.write_full(hs, C, 0)[1])
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    mutate(ts, C, [(0, 3), (3, 0)])
+    used_p = s.checkpoint(patch, snap.INCREMENTAL)
+    assert s.verify(patch, used_p) == 0
+    rc, exp, nd = oracle.write_patch(readback(ts), C, [oracle.chunk_hashes(h, C) for h in hs], 1, 0)
+    assert nd == 2 and np.array_equal(patch.view(used_p), exp)
+
+
+def test_stats_report_phases():
+    ts, _ = device_state([64 * 65536], seed=32)
+    s = make_set(ts, 65536)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    s.checkpoint(img, snap.FULL)
+    st = s.stats()
+    assert st["copy_ms"] > 0 and st["kernel_launches"] >= 3 and st["total_ms"] >= st["copy_ms"]
+    mutate(ts, 65536, [(0, 5)])
+    s.checkpoint(patch, snap.INCREMENTAL)
+    st = s.stats()
+    assert st["hash_ms"] > 0 and st["diff_ms"] > 0 and st["dirty_chunks"] == 1
+
+
 # ----------------------------------------------------------------- errors
 def test_restore_rejects_mismatch_and_bad_images():
     ts, _ = device_state([65536, 5000], seed=17)
