@@ -580,6 +580,16 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
         const uint8_t *dsrc = reinterpret_cast<const uint8_t *>(ad.ptr) + off;
         uint8_t *host_data = jb.layout == LAYOUT_IMAGE ? jb.host + ad.data_off + off
                                                        : jb.host + (ad.state_off + off - jb.window_off);
+        // every 16-byte access below needs 16-byte aligned device and host
+        // addresses; a misaligned tile is recorded and skipped, never issued
+        if ((((uintptr_t)dsrc | (uintptr_t)host_data) & 15u) && jb.op != OP_HASH && jb.op != OP_VERIFY) {
+            if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+            break;
+        }
+        if (((uintptr_t)dsrc & 15u) != 0u) {
+            if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+            break;
+        }
         bool ok = true;
         uint32_t h = 0;
         switch (jb.op) {
@@ -608,8 +618,12 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
             }
             break;
         case OP_GATHER_DIRTY: {
-            if (*reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) break;
-            uint8_t *dst = jb.host + jb.patch_data[k] + (tt - jb.dstart[k]) * C;
+            if (jb.cap_exceeded && *reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) break;
+            // IMAGE: the chunk's slot in the patch (dirty rank window_off + tt);
+            // PACKED: slot tt of a ring window of C-byte slots
+            uint8_t *dst = jb.layout == LAYOUT_IMAGE
+                               ? jb.host + jb.patch_data[k] + (jb.window_off + tt - jb.dstart[k]) * C
+                               : jb.host + tt * C;
             ok = gather_chunk_int(w, dsrc, L, (uint32_t)C, false, dst, cc, h);
             if (ok && (L & 4095u)) warp_zero(dst + L, up_page(L) - L, lane);
             break;

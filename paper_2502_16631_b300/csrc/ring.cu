@@ -1,12 +1,622 @@
-// Pageable images through the pinned ring (placeholder until the ring lands).
+// Pageable images through the set's pinned ring (snap_opts.ring_bytes).
+//
+// A checkpoint of device state larger than any pinned image the caller can
+// afford (tens of GB) streams through a fixed pinned, device-mapped ring
+// split into slots.  The chunk sequence is cut into windows whose bytes fit
+// one slot; for each window the persistent tile kernel gathers (and hashes)
+// its chunks into the slot in packed order, and host worker threads copy the
+// slot into the pageable image while the GPU fills the next slots.  Restore
+// runs the other way: workers fill slots from the image, the kernel scatters
+// them.  The pipeline is driven from the host only -- no kernel ever waits
+// on a host flag -- and slot reuse is ordered by one CUDA event per slot
+// and per-window host counters.  Every host wait is bounded by the call's
+// deadline.
 #include "snap.h"
+#include "snap_format.h"
 #include "runtime_internal.h"
 
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 namespace snapk {
-int ring_checkpoint(snap_set_s *, uint8_t *, uint64_t, int, uint64_t *, double, double, double) { return SNAP_EINVAL; }
-int ring_restore(snap_set_s *, const uint8_t *, uint64_t, const ImageHeader &, double, double, double)
+
+static inline uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
+
+// ------------------------------------------------------------ thread pool
+class Pool {
+public:
+    explicit Pool(int n)
+    {
+        for (int i = 0; i < n; ++i) th_.emplace_back([this] { run(); });
+    }
+    ~Pool()
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : th_) t.join();
+    }
+    void push(std::function<void()> f)
+    {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            q_.push_back(std::move(f));
+        }
+        cv_.notify_one();
+    }
+    int size() const { return (int)th_.size(); }
+
+private:
+    void run()
+    {
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
+                if (q_.empty()) return;
+                f = std::move(q_.front());
+                q_.pop_front();
+            }
+            f();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::deque<std::function<void()>> q_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    bool stop_ = false;
+};
+
+struct Ring {
+    uint8_t *host = nullptr;  // pinned, mapped
+    uint8_t *dev = nullptr;   // its device-visible address
+    uint64_t bytes = 0, slot_bytes = 0;
+    int slots = 0;
+    std::vector<cudaEvent_t> ev;  // one per slot: the last kernel that used it
+    Pool *pool = nullptr;
+    Job *d_jobs = nullptr;   // one job per slot (device)
+    Job *h_jobs = nullptr;   // pinned staging
+    unsigned long long *d_cursor = nullptr;  // one cursor per slot
+};
+
+void ring_free(snap_set_s *s)
 {
-    return SNAP_EINVAL;
+    Ring *r = s->ring;
+    if (!r) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    delete r->pool;
+    for (auto e : r->ev) cudaEventDestroy(e);
+    cudaFreeHost(r->host);
+    cudaFree(r->d_jobs);
+    cudaFreeHost(r->h_jobs);
+    cudaFree(r->d_cursor);
+    delete r;
+    s->ring = nullptr;
 }
-void ring_free(snap_set_s *) {}
+
+static int ring_get(snap_set_s *s, Ring **out)
+{
+    if (s->ring) {
+        *out = s->ring;
+        return SNAP_OK;
+    }
+    if (fault_injected("pinned_alloc")) return SNAP_ENOMEM;
+    auto *r = new (std::nothrow) Ring();
+    if (!r) return SNAP_ENOMEM;
+    uint64_t bytes = s->opts.ring_bytes;
+    int slots = 16;
+    while (slots > 2 && bytes / slots < 4 * (uint64_t)s->C) slots /= 2;
+    if (bytes / slots < s->C) bytes = (uint64_t)slots * s->C;
+    r->slots = slots;
+    r->slot_bytes = (bytes / slots) & ~uint64_t(4095u);
+    r->bytes = r->slot_bytes * slots;
+    cudaError_t e = cudaHostAlloc((void **)&r->host, r->bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e == cudaSuccess) r->dev = mapped_device_ptr(r->host);
+    if (e == cudaSuccess && !r->dev) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_jobs, sizeof(Job) * slots);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&r->h_jobs, sizeof(Job) * slots, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_cursor, sizeof(unsigned long long) * slots);
+    r->ev.assign(slots, nullptr);
+    for (int i = 0; i < slots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&r->ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->ring = r;
+        ring_free(s);
+        return SNAP_ENOMEM;
+    }
+    const int hw = (int)std::thread::hardware_concurrency();
+    r->pool = new Pool(std::max(2, std::min(12, hw > 2 ? hw - 2 : 2)));
+    s->ring = r;
+    *out = r;
+    return SNAP_OK;
+}
+
+// A window: global chunks [c0, c1) = concatenated-state bytes [b0, b1).
+struct Window {
+    uint64_t c0, c1, b0, b1;
+};
+
+static std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes)
+{
+    std::vector<Window> w;
+    Window cur{0, 0, 0, 0};
+    for (size_t k = 0; k < s->desc.size(); ++k) {
+        const AllocDesc &a = s->desc[k];
+        const uint64_t nk = (a.bytes + s->C - 1) / s->C;
+        for (uint64_t i = 0; i < nk; ++i) {
+            const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
+            const uint64_t b = a.state_off + i * s->C;
+            if (cur.c1 > cur.c0 && (b + L) - cur.b0 > slot_bytes) {
+                w.push_back(cur);
+                cur = Window{cur.c1, cur.c1, b, b};
+            }
+            if (cur.c1 == cur.c0) cur.b0 = b;
+            cur.c1 = a.chunk0 + i + 1;
+            cur.b1 = b + L;
+        }
+    }
+    if (cur.c1 > cur.c0) w.push_back(cur);
+    return w;
+}
+
+// Per-window completion counter shared by the host workers and the launcher.
+struct Progress {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<int> left;         // parts still running per window
+    std::vector<char> launched;    // launcher recorded the window's event
+    std::atomic<int> err{0};
+    int outstanding = 0;           // parts queued or running
+
+    void done(size_t w)
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        --left[w];
+        --outstanding;
+        cv.notify_all();
+    }
+    // wait until pred() with the deadline; false on timeout
+    template <class F>
+    bool wait(double deadline, F pred)
+    {
+        std::unique_lock<std::mutex> lk(mu);
+        while (!pred()) {
+            if (now_ms() > deadline) return false;
+            cv.wait_for(lk, std::chrono::milliseconds(2));
+        }
+        return true;
+    }
+};
+
+// Copy between the packed window [b0, b1) of the slot and the image's data
+// regions, restricted to the part [p0, p1) of the window.
+static void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0,
+                             uint64_t p1, bool to_image)
+{
+    // allocations overlapping [w.b0 + p0, w.b0 + p1)
+    const uint64_t lo = w.b0 + p0, hi = w.b0 + p1;
+    size_t k = 0;
+    {
+        size_t a = 0, b = s->desc.size();
+        while (b - a > 1) {  // last allocation with state_off <= lo
+            const size_t m = (a + b) / 2;
+            if (s->desc[m].state_off <= lo) a = m; else b = m;
+        }
+        k = a;
+    }
+    for (; k < s->desc.size() && s->desc[k].state_off < hi; ++k) {
+        const AllocDesc &a = s->desc[k];
+        const uint64_t x0 = std::max(lo, a.state_off), x1 = std::min(hi, a.state_off + a.bytes);
+        if (x1 <= x0) continue;
+        uint8_t *img = image + a.data_off + (x0 - a.state_off);
+        uint8_t *sl = slot + (x0 - w.b0);
+        if (to_image) std::memcpy(img, sl, x1 - x0);
+        else std::memcpy(sl, img, x1 - x0);
+    }
+}
+
+static bool poll_event(cudaEvent_t e, double deadline)
+{
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(e);
+        if (q == cudaSuccess) return true;
+        if (q != cudaErrorNotReady || now_ms() > deadline) return false;
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+static Job window_job(const snap_set_s *s, Ring *r, int slot, uint32_t op, const Window &w, uint32_t *hash_out)
+{
+    Job j{};
+    j.allocs = s->d_allocs;
+    j.n_allocs = s->desc.size();
+    j.chunk_bytes = s->C;
+    j.tile_begin = w.c0;
+    j.n_tiles = w.c1 - w.c0;
+    j.host = r->dev + (uint64_t)slot * r->slot_bytes;
+    j.window_off = w.b0;
+    j.op = op;
+    j.layout = LAYOUT_PACKED;
+    j.hash_out = hash_out;
+    j.res = &s->d_cb->res;
+    return j;
+}
+
+// Launch one window's tile kernel into its slot and record the slot event.
+static cudaError_t launch_window(snap_set_s *s, Ring *r, int slot, const Job &j, const TileShape &sh,
+                                 const CombineConsts &cc)
+{
+    r->h_jobs[slot] = j;
+    cudaError_t e = cudaMemcpyAsync(r->d_jobs + slot, r->h_jobs + slot, sizeof(Job), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_cursor + slot, 0, sizeof(unsigned long long), s->st);
+    if (e == cudaSuccess) e = launch_tiles(r->d_jobs + slot, 1, r->d_cursor + slot, cc, sh, &s->d_cb->res, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev[slot], s->st);
+    return e;
+}
+
+static uint64_t parts_for(uint64_t bytes, int threads)
+{
+    const uint64_t p = std::max<uint64_t>(1, bytes / (8ull << 20));  // about 8 MiB per part
+    return std::min<uint64_t>(p, (uint64_t)threads * 2);
+}
+
+// Wait for every queued worker task (bounded); used on every exit path so
+// that no task outlives the caller's buffers.
+static void drain(Progress &pg)
+{
+    std::unique_lock<std::mutex> lk(pg.mu);
+    while (pg.outstanding > 0) pg.cv.wait_for(lk, std::chrono::milliseconds(2));
+}
+
+// --------------------------------------------------------------- checkpoint
+static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, double deadline, int cur, snap_stats &st)
+{
+    if (cap < s->full_bytes) return SNAP_EINVAL;
+    const std::vector<Window> win = make_windows(s, r->slot_bytes);
+    const size_t W = win.size();
+    Progress pg;
+    pg.left.assign(W, 0);
+    pg.launched.assign(W, 0);
+    std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
+    s->h_cb->res.first_bad = ~0ull;
+    cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, offsetof(CallBlock, jobs), cudaMemcpyHostToDevice, s->st);
+    const TileShape sh = s->shape[SHAPE_GATHER];
+    const CombineConsts cc = make_combine_consts(s->C, sh.piece);
+    int rc = SNAP_OK;
+    const double tk0 = now_ms();
+    for (size_t w = 0; w < W && e == cudaSuccess && rc == SNAP_OK; ++w) {
+        const int slot = (int)(w % r->slots);
+        if (w >= (size_t)r->slots) {
+            const size_t prev = w - r->slots;  // its copy-out must be finished
+            if (!pg.wait(deadline, [&] { return pg.left[prev] == 0; })) rc = SNAP_ETIMEDOUT;
+            if (pg.err) rc = pg.err;
+            if (rc) break;
+        }
+        e = launch_window(s, r, slot, window_job(s, r, slot, OP_GATHER, win[w], s->d_hash[cur]), sh, cc);
+        if (e != cudaSuccess) break;
+        const uint64_t nbytes = win[w].b1 - win[w].b0;
+        const uint64_t np = parts_for(nbytes, r->pool->size());
+        {
+            std::lock_guard<std::mutex> lk(pg.mu);
+            pg.left[w] = (int)np;
+            pg.outstanding += (int)np;
+        }
+        for (uint64_t p = 0; p < np; ++p) {
+            const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
+            r->pool->push([&, w, slot, p0, p1] {
+                if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+                if (!pg.err)
+                    copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, image, p0, p1, true);
+                pg.done(w);
+            });
+        }
+    }
+    if (e != cudaSuccess && rc == SNAP_OK) rc = cuda_status(e);
+    drain(pg);
+    if (rc == SNAP_OK && pg.err) rc = pg.err;
+    if (rc) return rc;
+    // hashes and kernel flags
+    if (s->n_chunks)
+        e = cudaMemcpyAsync(s->h_hash_stage, s->d_hash[cur], s->n_chunks * 4, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->h_res->err) return SNAP_ECUDA;
+    st.copy_ms = now_ms() - tk0;
+    // metadata: records, hashes and padding (the data regions are written)
+    for (size_t k = 0; k < s->desc.size(); ++k) {
+        const AllocDesc &a = s->desc[k];
+        const uint64_t nk = (a.bytes + s->C - 1) / s->C;
+        const uint64_t rec[4] = {a.bytes, nk, a.data_off, 0};
+        std::memcpy(image + a.rec_off, rec, 32);
+        std::memcpy(image + a.rec_off + 32, s->h_hash_stage + a.chunk0, 4 * nk);
+        std::memset(image + a.rec_off + 32 + 4 * nk, 0, a.data_off - (a.rec_off + 32 + 4 * nk));
+        std::memset(image + a.data_off + a.bytes, 0, upg(a.data_off + a.bytes) - (a.data_off + a.bytes));
+    }
+    st.image_bytes = s->full_bytes;
+    st.dirty_chunks = s->n_chunks;
+    st.kernel_launches = W;
+    return SNAP_OK;
+}
+
+// Incremental into a pageable patch: device hash + diff + layout as in the
+// direct path, metadata written by the host from the copied-back tables, and
+// the dirty chunks streamed through the ring one C-byte slot each.
+static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, double deadline, int cur,
+                            uint64_t *used, snap_stats &st)
+{
+    std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
+    s->h_cb->res.first_bad = ~0ull;
+    s->h_cb->cp.image = nullptr;
+    s->h_cb->cp.cap = cap;
+    Job jh{};
+    jh.allocs = s->d_allocs;
+    jh.n_allocs = s->desc.size();
+    jh.chunk_bytes = s->C;
+    jh.n_tiles = s->n_chunks;
+    jh.op = OP_HASH;
+    jh.hash_out = s->d_hash[cur];
+    jh.res = &s->d_cb->res;
+    s->h_cb->jobs[0] = jh;
+    const TileShape shh = s->shape[SHAPE_HASH];
+    const CombineConsts cch = make_combine_consts(s->C, shh.piece);
+    const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
+    const double th0 = now_ms();
+    cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, offsetof(CallBlock, jobs) + sizeof(Job), cudaMemcpyHostToDevice,
+                                    s->st);
+    if (e == cudaSuccess && s->n_chunks)
+        e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cch, shh, &s->d_cb->res, s->st);
+    if (e == cudaSuccess)
+        e = launch_diff(curp, prevp, s->n_chunks, s->d_blockcnt, s->d_blockoff, s->d_dlist, &s->d_cb->res, s->st);
+    if (e == cudaSuccess)
+        e = launch_patch_layout(s->d_allocs, s->desc.size(), s->C, s->d_dlist, s->d_patch_rec, s->d_patch_data,
+                                s->d_dstart, &s->d_cb->cp, &s->d_cb->res, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->h_res->err) return SNAP_ECUDA;
+    if (s->h_res->cap_exceeded) return SNAP_EINVAL;
+    st.hash_ms = now_ms() - th0;
+    const uint64_t nd = s->h_res->n_dirty, na = s->desc.size();
+    std::vector<uint32_t> dl(nd ? nd : 1);
+    std::vector<uint64_t> prec(na ? na : 1), pdat(na ? na : 1), dst(na + 1);
+    if (nd) e = cudaMemcpy(dl.data(), s->d_dlist, nd * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && na) e = cudaMemcpy(prec.data(), s->d_patch_rec, na * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && na) e = cudaMemcpy(pdat.data(), s->d_patch_data, na * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(dst.data(), s->d_dstart, (na + 1) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && s->n_chunks)
+        e = cudaMemcpy(s->h_hash_stage, curp, s->n_chunks * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    // metadata
+    for (size_t k = 0; k < na; ++k) {
+        const AllocDesc &a = s->desc[k];
+        const uint64_t nk = (a.bytes + s->C - 1) / s->C;
+        const uint64_t ndk = dst[k + 1] - dst[k];
+        const uint64_t rec[4] = {a.bytes, nk, pdat[k], 0};
+        uint8_t *p = image + prec[k];
+        std::memcpy(p, rec, 32);
+        std::memcpy(p + 32, s->h_hash_stage + a.chunk0, 4 * nk);
+        const uint32_t n32 = (uint32_t)ndk;
+        std::memcpy(p + 32 + 4 * nk, &n32, 4);
+        for (uint64_t j = 0; j < ndk; ++j) {
+            const uint32_t idx = dl[dst[k] + j] - (uint32_t)a.chunk0;
+            std::memcpy(p + 36 + 4 * nk + 4 * j, &idx, 4);
+        }
+        const uint64_t z = prec[k] + 36 + 4 * nk + 4 * ndk;
+        std::memset(image + z, 0, pdat[k] - z);
+    }
+    // dirty data: windows of whole C-byte slots over the dirty ranks
+    const uint64_t per = r->slot_bytes / s->C;
+    const size_t W = (size_t)((nd + per - 1) / per);
+    Progress pg;
+    pg.left.assign(W, 0);
+    const TileShape shg = s->shape[SHAPE_GATHER];
+    const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
+    const double tc0 = now_ms();
+    int rc = SNAP_OK;
+    for (size_t w = 0; w < W && rc == SNAP_OK; ++w) {
+        const int slot = (int)(w % r->slots);
+        if (w >= (size_t)r->slots) {
+            const size_t prev = w - r->slots;
+            if (!pg.wait(deadline, [&] { return pg.left[prev] == 0; })) rc = SNAP_ETIMEDOUT;
+            if (pg.err) rc = pg.err;
+            if (rc) break;
+        }
+        const uint64_t r0 = w * per, r1 = std::min<uint64_t>(nd, r0 + per);
+        Job j{};
+        j.allocs = s->d_allocs;
+        j.n_allocs = na;
+        j.chunk_bytes = s->C;
+        j.tile_list = s->d_dlist + r0;
+        j.n_tiles = r1 - r0;
+        j.host = r->dev + (uint64_t)slot * r->slot_bytes;
+        j.op = OP_GATHER_DIRTY;
+        j.layout = LAYOUT_PACKED;
+        j.res = &s->d_cb->res;
+        e = launch_window(s, r, slot, j, shg, ccg);
+        if (e != cudaSuccess) {
+            rc = cuda_status(e);
+            break;
+        }
+        {
+            std::lock_guard<std::mutex> lk(pg.mu);
+            pg.left[w] = 1;
+            pg.outstanding += 1;
+        }
+        r->pool->push([&, w, slot, r0, r1] {
+            if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+            if (!pg.err) {
+                const uint8_t *sl = r->host + (uint64_t)slot * r->slot_bytes;
+                size_t k = 0;
+                for (uint64_t q = r0; q < r1; ++q) {
+                    const uint64_t c = dl[q];
+                    while (k + 1 < na && s->desc[k + 1].chunk0 <= c) ++k;
+                    while (k > 0 && s->desc[k].chunk0 > c) --k;
+                    const AllocDesc &a = s->desc[k];
+                    const uint64_t i = c - a.chunk0;
+                    const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
+                    std::memcpy(image + pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
+                }
+            }
+            pg.done(w);
+        });
+    }
+    drain(pg);
+    if (rc == SNAP_OK && pg.err) rc = pg.err;
+    if (rc) return rc;
+    e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->h_res->err) return SNAP_ECUDA;
+    st.copy_ms = now_ms() - tc0;
+    *used = s->h_res->patch_bytes;
+    st.image_bytes = *used;
+    st.dirty_chunks = nd;
+    st.kernel_launches = 5 + W;
+    return SNAP_OK;
+}
+
+int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
+                    double deadline)
+{
+    Ring *r = nullptr;
+    int rc = ring_get(s, &r);
+    if (rc) return rc;
+    const int cur = 1 - s->prev_idx;
+    const uint64_t gen = s->next_gen;
+    snap_stats st{};
+    if (mode == SNAP_FULL) {
+        rc = ring_full(s, r, image, cap, deadline, cur, st);
+        if (rc) return rc;
+        write_header(image, SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(), s->total_bytes, gen, 0);
+        *used = s->full_bytes;
+    } else {
+        rc = ring_incremental(s, r, image, cap, deadline, cur, used, st);
+        if (rc) return rc;
+        write_header(image, SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C, s->desc.size(),
+                     s->total_bytes, gen, s->base_gen);
+    }
+    s->prev_idx = cur;
+    s->has_base = true;
+    s->base_gen = gen;
+    s->next_gen = gen + 1;
+    st.state_bytes = s->total_bytes;
+    st.total_chunks = s->n_chunks;
+    st.generation = gen;
+    st.quiesce_ms = tq - t0;
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
+// ------------------------------------------------------------------ restore
+int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const ImageHeader &h, double t0, double tq,
+                 double deadline)
+{
+    (void)bytes;
+    Ring *r = nullptr;
+    int rc = ring_get(s, &r);
+    if (rc) return rc;
+    const int cur = 1 - s->prev_idx;
+    const std::vector<Window> win = make_windows(s, r->slot_bytes);
+    const size_t W = win.size();
+    Progress pg;
+    pg.left.assign(W, 0);
+    pg.launched.assign(W, 0);
+    std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
+    cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, offsetof(CallBlock, jobs), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess && s->n_chunks)
+        e = cudaMemcpyAsync(s->d_hash[cur], s->h_hash_stage, s->n_chunks * 4, cudaMemcpyHostToDevice, s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    const TileShape sh = s->shape[SHAPE_SCATTER];
+    const CombineConsts cc = make_combine_consts(s->C, sh.piece);
+    const double tc0 = now_ms();
+    uint8_t *img = const_cast<uint8_t *>(image);  // read only: copies run image -> slot
+
+    // queue the fill of window w: it waits for the kernel of window w - slots
+    auto queue_fill = [&](size_t w) {
+        const int slot = (int)(w % r->slots);
+        const uint64_t nbytes = win[w].b1 - win[w].b0;
+        const uint64_t np = parts_for(nbytes, r->pool->size());
+        {
+            std::lock_guard<std::mutex> lk(pg.mu);
+            pg.left[w] = (int)np;
+            pg.outstanding += (int)np;
+        }
+        for (uint64_t p = 0; p < np; ++p) {
+            const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
+            r->pool->push([&, w, slot, p0, p1] {
+                if (w >= (size_t)r->slots && !pg.err) {
+                    const size_t prev = w - r->slots;
+                    if (!pg.wait(deadline, [&] { return pg.launched[prev] != 0; })) pg.err = SNAP_ETIMEDOUT;
+                    if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+                }
+                if (!pg.err)
+                    copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, img, p0, p1, false);
+                pg.done(w);
+            });
+        }
+    };
+    for (size_t w = 0; w < std::min<size_t>(W, r->slots); ++w) queue_fill(w);
+    for (size_t w = 0; w < W && rc == SNAP_OK; ++w) {
+        const int slot = (int)(w % r->slots);
+        if (!pg.wait(deadline, [&] { return pg.left[w] == 0; })) rc = SNAP_ETIMEDOUT;
+        if (pg.err) rc = pg.err;
+        if (rc) break;
+        e = launch_window(s, r, slot, window_job(s, r, slot, OP_SCATTER, win[w], nullptr), sh, cc);
+        if (e != cudaSuccess) {
+            rc = cuda_status(e);
+            break;
+        }
+        {
+            std::lock_guard<std::mutex> lk(pg.mu);
+            pg.launched[w] = 1;
+            pg.cv.notify_all();
+        }
+        if (w + r->slots < W) queue_fill(w + r->slots);
+    }
+    if (rc) {
+        pg.err = rc;  // release fills waiting on windows that will not launch
+        {
+            std::lock_guard<std::mutex> lk(pg.mu);
+            std::fill(pg.launched.begin(), pg.launched.end(), 1);
+            pg.cv.notify_all();
+        }
+    }
+    drain(pg);
+    if (rc) {
+        cudaStreamSynchronize(s->st);
+        return rc;
+    }
+    e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->h_res->err) return SNAP_ECUDA;
+    s->prev_idx = cur;
+    s->has_base = true;
+    s->base_gen = h.generation;
+    s->next_gen = h.generation + 1;
+    snap_stats st{};
+    st.state_bytes = s->total_bytes;
+    st.image_bytes = s->full_bytes;
+    st.total_chunks = s->n_chunks;
+    st.generation = h.generation;
+    st.quiesce_ms = tq - t0;
+    st.copy_ms = now_ms() - tc0;
+    st.kernel_launches = W;
+    st.total_ms = now_ms() - t0;
+    s->last = st;
+    return SNAP_OK;
+}
+
 }  // namespace snapk

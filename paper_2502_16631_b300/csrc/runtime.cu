@@ -190,7 +190,7 @@ static int build_layout(snap_set_s *s)
     s->has_base = false;
     const uint64_t C = s->C;
     s->desc.resize(s->allocs.size());
-    uint64_t off = SNAP_IMG_HEADER_BYTES, chunk = 0, state = 0;
+    uint64_t off = SNAP_IMG_HEADER_BYTES, chunk = 0, state = 0, pack = 0;
     for (size_t k = 0; k < s->allocs.size(); ++k) {
         AllocDesc &a = s->desc[k];
         a.ptr = (uint64_t)(uintptr_t)s->allocs[k].ptr;
@@ -199,7 +199,10 @@ static int build_layout(snap_set_s *s)
         a.chunk0 = chunk;
         a.rec_off = off;
         a.data_off = up_page(off + 32 + 4 * nk);
-        a.state_off = state;
+        // packed (ring) offset: every allocation starts 256-byte aligned so
+        // that the kernels' 16-byte accesses to a ring slot stay aligned
+        a.state_off = pack;
+        pack = (pack + a.bytes + 255u) & ~uint64_t(255u);
         off = up_page(a.data_off + a.bytes);
         chunk += nk;
         state += a.bytes;

@@ -46,7 +46,7 @@ struct Ring;
 struct snap_set_s {
     int device = 0;
     int sms = 148;
-    char gpu_name[128] = {0};
+    char gpu_name[256] = {0};
     uint64_t C = 65536;
     uint32_t timeout_ms = 10000;
     cudaStream_t user_stream = nullptr;  // the caller's stream (quiesced)

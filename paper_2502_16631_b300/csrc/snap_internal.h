@@ -14,7 +14,8 @@ struct AllocDesc {
     uint64_t chunk0;     // global index of its first chunk
     uint64_t rec_off;    // full image: offset of its 32-byte record
     uint64_t data_off;   // full image: offset of its data (4 KiB aligned)
-    uint64_t state_off;  // offset in the concatenation of all allocations
+    uint64_t state_off;  // offset in the packed concatenation of all allocations
+                         // (each allocation starts on a 256-byte boundary)
 };
 
 // What a job does with each of its chunk tiles.

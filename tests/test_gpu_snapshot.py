@@ -265,6 +265,36 @@ def test_incremental_errors_keep_base():
     assert s.stats()["dirty_chunks"] == 8 and used > 8 * C
 
 
+# ----------------------------------------------- pageable images via the ring
+@pytest.mark.parametrize("C,ring", [(4096, 1 << 20), (65536, 2 << 20)])
+def test_ring_pageable_images(C, ring):
+    """Images in ordinary (pageable) host memory stream through a small
+    pinned ring: many windows, slot reuse, ragged allocations."""
+    sizes = [8 * C + 100, 3 * C, 1, 0, 200000, C + 1, 70 * C]
+    ts, hs = device_state(sizes, seed=41)
+    s = make_set(ts, C, ring_bytes=ring)
+    full = np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8)  # pageable
+    used = s.checkpoint(full, snap.FULL)
+    assert np.array_equal(full[:used], oracle.write_full(hs, C, 0)[1])
+    assert s.verify(full, used) == 0
+    # incremental into a pageable patch
+    nch = [(n + C - 1) // C for n in sizes]
+    dirty = [(0, 0), (0, nch[0] - 1), (4, 2), (6, 5), (6, 6), (6, 69), (2, 0)]
+    mutate(ts, C, dirty)
+    patch = np.full(s.image_bytes(snap.INCREMENTAL), 0x5A, dtype=np.uint8)
+    used_p = s.checkpoint(patch, snap.INCREMENTAL)
+    cur = readback(ts)
+    rc, exp, nd = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in hs], 1, 0)
+    assert nd == len(set(dirty)) and np.array_equal(patch[:used_p], exp)
+    # restore the generation-0 image from pageable memory
+    for t in ts:
+        t.zero_()
+    s.restore(full, used)
+    for a, b in zip(readback(ts), hs):
+        assert np.array_equal(a, b)
+    assert s.committed_hashes(sum(nch))[1] == 0
+
+
 # ------------------------------------------------------------- autotuner
 @pytest.mark.parametrize("C", [4096, 65536])
 def test_autotune_every_shape_agrees_then_parity(C):
