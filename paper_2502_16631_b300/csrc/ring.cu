@@ -14,6 +14,7 @@
 #include "snap.h"
 #include "snap_format.h"
 #include "runtime_internal.h"
+#include "host_pool.h"
 
 #include <algorithm>
 #include <atomic>
@@ -28,54 +29,6 @@
 namespace snapk {
 
 static inline uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
-
-// ------------------------------------------------------------ thread pool
-class Pool {
-public:
-    explicit Pool(int n)
-    {
-        for (int i = 0; i < n; ++i) th_.emplace_back([this] { run(); });
-    }
-    ~Pool()
-    {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            stop_ = true;
-        }
-        cv_.notify_all();
-        for (auto &t : th_) t.join();
-    }
-    void push(std::function<void()> f)
-    {
-        {
-            std::lock_guard<std::mutex> lk(mu_);
-            q_.push_back(std::move(f));
-        }
-        cv_.notify_one();
-    }
-    int size() const { return (int)th_.size(); }
-
-private:
-    void run()
-    {
-        for (;;) {
-            std::function<void()> f;
-            {
-                std::unique_lock<std::mutex> lk(mu_);
-                cv_.wait(lk, [this] { return stop_ || !q_.empty(); });
-                if (q_.empty()) return;
-                f = std::move(q_.front());
-                q_.pop_front();
-            }
-            f();
-        }
-    }
-    std::vector<std::thread> th_;
-    std::deque<std::function<void()>> q_;
-    std::mutex mu_;
-    std::condition_variable cv_;
-    bool stop_ = false;
-};
 
 struct Ring {
     uint8_t *host = nullptr;  // pinned, mapped
@@ -141,12 +94,7 @@ static int ring_get(snap_set_s *s, Ring **out)
     return SNAP_OK;
 }
 
-// A window: global chunks [c0, c1) = concatenated-state bytes [b0, b1).
-struct Window {
-    uint64_t c0, c1, b0, b1;
-};
-
-static std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes)
+std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes)
 {
     std::vector<Window> w;
     Window cur{0, 0, 0, 0};
@@ -200,7 +148,7 @@ struct Progress {
 
 // Copy between the packed window [b0, b1) of the slot and the image's data
 // regions, restricted to the part [p0, p1) of the window.
-static void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0,
+void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0,
                              uint64_t p1, bool to_image)
 {
     // allocations overlapping [w.b0 + p0, w.b0 + p1)
@@ -225,7 +173,7 @@ static void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot
     }
 }
 
-static bool poll_event(cudaEvent_t e, double deadline)
+bool poll_event(cudaEvent_t e, double deadline)
 {
     for (;;) {
         const cudaError_t q = cudaEventQuery(e);
@@ -264,7 +212,7 @@ static cudaError_t launch_window(snap_set_s *s, Ring *r, int slot, const Job &j,
     return e;
 }
 
-static uint64_t parts_for(uint64_t bytes, int threads)
+uint64_t parts_for(uint64_t bytes, int threads)
 {
     const uint64_t p = std::max<uint64_t>(1, bytes / (8ull << 20));  // about 8 MiB per part
     return std::min<uint64_t>(p, (uint64_t)threads * 2);

@@ -183,7 +183,7 @@ static void free_device(snap_set_s *s)
     s->h_hash_stage = nullptr;
 }
 
-static int build_layout(snap_set_s *s)
+int build_layout(snap_set_s *s)
 {
     if (!s->layout_dirty) return SNAP_OK;
     free_device(s);

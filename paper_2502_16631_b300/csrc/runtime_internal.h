@@ -114,4 +114,17 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
                  double deadline);
 void ring_free(snap_set_s *s);
 
+// A window: global chunks [c0, c1) = packed-state bytes [b0, b1).
+struct Window {
+    uint64_t c0, c1, b0, b1;
+};
+std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes);
+void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0, uint64_t p1,
+                      bool to_image);
+bool poll_event(cudaEvent_t e, double deadline);
+uint64_t parts_for(uint64_t bytes, int threads);
+
+// (Re)build a set's device layout after registrations (runtime.cu).
+int build_layout(snap_set_s *s);
+
 }  // namespace snapk
