@@ -53,6 +53,14 @@ def parse():
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-bytes", type=int, default=512 * MiB)
+    p.add_argument("--workload", default="gpt2",
+                   choices=["gpt2", "random64m", "incr20g", "llama7b", "serving"],
+                   help="gpt2: GPT-2-small training state (default); random64m: 16 random allocations, "
+                        "64 MiB; incr20g: 20 GiB incremental at 1/10/50%% dirty with the chunk-size sweep; "
+                        "llama7b: 115.8 GB Llama-7B state through the pinned ring; serving: 32 tenants, "
+                        "Poisson arrivals")
+    p.add_argument("--arrivals", type=int, default=1200, help="serving: requests")
+    p.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     return p.parse_args()
 
 
@@ -467,6 +475,413 @@ def run_snap(args, rank, world, local, pg):
         print(json.dumps(line))
 
 
+# ------------------------------------------------------ further workloads
+def _line(args, world, value, ms, config, extra):
+    d = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def run_random64m(args, rank, world, local, pg):
+    """16 allocations log-uniform in [64 KiB, 16 MiB], exactly 64 MiB of
+    xorshift64* bytes; step = full checkpoint + restore."""
+    import torch
+    import oracle
+    import paper_2502_16631_b300 as snap
+    sizes = workloads.config1_sizes(args.seed)
+    host = [workloads.xorshift_bytes(n, args.seed, k) for k, n in enumerate(sizes)]
+    ts = [torch.from_numpy(h).cuda() for h in host]
+    B = sum(sizes)
+    s = snap.Set(chunk_bytes=UNIT)
+    for t in ts:
+        s.register(t)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    ok_img = bool(np.array_equal(img.view(used), oracle.write_full(host, UNIT, 0)[1]))
+    s.restore(img, used)
+    ok_rest = all(np.array_equal(t.cpu().numpy(), h) for t, h in zip(ts, host))
+    for _ in range(max(3, args.warmup)):
+        s.checkpoint(img, snap.FULL)
+        s.restore(img, used)
+    peaks = link_peak(torch)
+    clocks = ClockSampler(local)
+    clocks.start()
+    g, sc, kern = [], [], 0
+    a, b = _ev(), _ev()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        s.checkpoint(img, snap.FULL)
+        st = s.stats()
+        g.append(st["copy_ms"])
+        kern += st["kernel_launches"]
+        s.restore(img, used)
+        st = s.stats()
+        sc.append(st["copy_ms"])
+        kern += st["kernel_launches"]
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    ach = B / (statistics.mean(g) * 1e-3) / 1e9
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < 10 and n < 20:
+        rc, im = oracle.write_full(host, UNIT, 0)
+        oracle.restore(im, sizes)
+        n += 1
+    cpu = {"value": 2 * B / ((time.perf_counter() - t0) / n) / 1e9, "unit": "GB/s",
+           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": "the whole 64 MiB state, %d full image writes + restores" % n}
+    print(json.dumps(_line(args, world, 2 * B / (ms * 1e-3) / 1e9, ms,
+                           {"workload": "16 random allocations, log-uniform [64 KiB, 16 MiB], 67,108,864 B, "
+                                        "64 KiB chunks", "step": "full checkpoint + restore",
+                            "l2": "64 MiB fits in L2: steps run back to back without a flush"},
+                           {"roofline": {"bound": "host_link", "kernel": "snap_tiles (OP_GATHER)", "achieved": ach,
+                                         "peak": peaks["d2h"], "unit": "GB/s", "frac": ach / peaks["d2h"]},
+                            "parity": {"image_equals_oracle": ok_img, "restore_equals_original": ok_rest},
+                            "cpu_baseline": cpu, "clocks": clk, "gpu_launches": kern,
+                            "e2e": {"value": 2 * B / (ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": B,
+                                    "d2h_bytes_per_step": used}})))
+
+
+def run_incr20g(args, rank, world, local, pg):
+    """20 GiB in 2,000 allocations; incremental checkpoints at 1, 10 and 50 %
+    clustered dirty chunks (10 consecutive steps each), for every chunk size
+    of the autotuner's sweep (16 KiB - 1 MiB); graph-captured."""
+    import torch
+    import paper_2502_16631_b300 as snap
+    sizes = workloads.config3_sizes(args.seed)
+    B = sum(sizes)
+    align = 1 << 20
+    starts, off = [], 0
+    for n in sizes:
+        starts.append(off)
+        off += (n + align - 1) // align * align
+    arena = torch.empty(off, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(args.seed)
+    step = 1 << 30
+    for p in range(0, off, step):
+        q = min(off, p + step)
+        arena[p:q].copy_(torch.randint(0, 256, (q - p,), dtype=torch.uint8, device="cuda", generator=g))
+    views = [arena[s0: s0 + n] for s0, n in zip(starts, sizes)]
+    grid = arena.view(-1, UNIT)
+    fracs = [0.01, 0.10, 0.50]
+    units = {f: torch.from_numpy(dirty_units(sizes, starts, f, args.seed + int(f * 1000))).cuda() for f in fracs}
+    chunks = [16 * KiB, 32 * KiB, 64 * KiB, 128 * KiB, 256 * KiB, 512 * KiB, 1024 * KiB]
+    sets = {}
+    cap_full = cap_patch = 0
+    for C in chunks:
+        s = snap.Set(chunk_bytes=C)
+        for v in views:
+            s.register(v)
+        sets[C] = s
+        cap_full = max(cap_full, s.image_bytes(snap.FULL))
+        cap_patch = max(cap_patch, s.image_bytes(snap.INCREMENTAL))
+    full = snap.HostBuffer(cap_full)
+    patch = snap.HostBuffer(cap_patch)
+    # plain form: one cudaMemcpyAsync per allocation, full copy
+    s64 = sets[64 * KiB]
+    s64.plain_checkpoint(full)
+    plain = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        s64.plain_checkpoint(full)
+        plain.append(time.perf_counter() - t0)
+    plain_gbs = B / min(plain) / 1e9
+    table, tune, kern = {}, {}, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    for C in chunks:
+        s = sets[C]
+        tune[C] = s.autotune(snap.INCREMENTAL)
+        s.checkpoint(full, snap.FULL)
+        table[C] = {}
+        for f in fracs:
+            times, dirty, hashms = [], [], []
+            for i in range(3 + 10):
+                grid[units[f]] ^= 0x5A  # the training step: every byte of each chosen unit changes
+                torch.cuda.synchronize()
+                a, b = _ev(), _ev()
+                a.record()
+                used = s.checkpoint(patch, snap.INCREMENTAL)
+                b.record()
+                torch.cuda.synchronize()
+                st = s.stats()
+                if i >= 3:
+                    times.append(a.elapsed_time(b))
+                    dirty.append(st["dirty_chunks"])
+                    hashms.append(st["hash_ms"])
+                    kern += st["kernel_launches"]
+            assert s.verify(patch, used) == 0
+            ms = statistics.median(times)
+            table[C][f] = {"ms": ms, "effective_gbs": B / (ms * 1e-3) / 1e9, "dirty_chunks": int(statistics.median(dirty)),
+                           "hash_ms": statistics.median(hashms), "vs_plain_full": (B / (ms * 1e-3) / 1e9) / plain_gbs}
+    clk = clocks.stop()
+    best = {f: max(chunks, key=lambda C: table[C][f]["effective_gbs"]) for f in fracs}
+    v10 = table[best[0.10]][0.10]
+    hash_best = min(table[C][0.01]["hash_ms"] for C in chunks)
+    pk = measured_peaks().get("hbm_gbs", 6400.0)
+    out = _line(args, world, v10["effective_gbs"], v10["ms"],
+                {"workload": "20 GiB in 2,000 allocations log-uniform [4 KiB, 256 MiB], random bytes; clustered "
+                             "dirty runs (mean 16 x 64 KiB)", "dirty_frac": 0.10, "chunk_bytes": best[0.10],
+                 "l2": "20 GiB state, larger than L2"},
+                {"incremental": {str(C // KiB) + "KiB": {str(int(f * 100)) + "%": table[C][f] for f in fracs}
+                                 for C in chunks},
+                 "autotuned_chunk": {str(int(f * 100)) + "%": best[f] // KiB for f in fracs},
+                 "autotuned_shape": {str(C // KiB) + "KiB": tune[C] for C in chunks},
+                 "speedup_vs_plain_full": {str(int(f * 100)) + "%": table[best[f]][f]["vs_plain_full"] for f in fracs},
+                 "plain_full_gbs": plain_gbs,
+                 "roofline": {"bound": "hbm", "kernel": "snap_tiles (OP_HASH)", "achieved": B / (hash_best * 1e-3) / 1e9,
+                              "peak": pk, "unit": "GB/s", "frac": B / (hash_best * 1e-3) / 1e9 / pk,
+                              "note": "hash pass of the 1% case (dirty copy negligible)"},
+                 "gpu_launches": kern, "clocks": clk})
+    print(json.dumps(out))
+
+
+def run_llama7b(args, rank, world, local, pg):
+    """Llama-7B-shaped state (bf16 W, fp32 master/m/v, 20 GiB bf16
+    activations, 115,812,655,104 B): full checkpoint through the 4 GiB pinned
+    ring into a pageable image; restore into freshly allocated buffers."""
+    import mmap
+    import torch
+    import oracle
+    import paper_2502_16631_b300 as snap
+    spec = workloads.llama7b_state_spec()
+    sizes = workloads.spec_bytes(spec)
+    B = sum(sizes)
+
+    def fresh():
+        return [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+
+    ts = fresh()
+    workloads.torch_fill_spec(ts, spec, seed=args.seed)
+    s = snap.Set(chunk_bytes=UNIT, ring_bytes=4 * GiB)
+    for t in ts:
+        s.register(t)
+    s.prepare(layout=True, ring=True)
+    nimg = s.image_bytes(snap.FULL)
+    t0 = time.perf_counter()
+    m = mmap.mmap(-1, nimg, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS | getattr(mmap, "MAP_POPULATE", 0))
+    img = np.frombuffer(m, dtype=np.uint8)
+    populate_s = time.perf_counter() - t0
+    # sampled chunks for parity at full size
+    rng = np.random.default_rng(args.seed)
+    nch = [(n + UNIT - 1) // UNIT for n in sizes]
+    c0 = np.concatenate([[0], np.cumsum(nch)])
+    picks = sorted(set(int(x) for x in rng.integers(0, c0[-1], 48)) | {int(c0[-1] - 1)})
+    samples = []
+    for c in picks:
+        k = int(np.searchsorted(c0, c, side="right") - 1)
+        i = c - int(c0[k])
+        lo, hi = i * UNIT, min((i + 1) * UNIT, sizes[k])
+        samples.append((k, i, lo, hi, ts[k][lo:hi].cpu().numpy().copy()))
+    ck, rs = [], []
+    peaks = link_peak(torch)
+    clocks = ClockSampler(local)
+    for step in range(max(1, args.warmup) + args.steps):
+        timed = step >= max(1, args.warmup)
+        if timed and not ck:
+            clocks.start()
+        t0 = time.perf_counter()
+        used = s.checkpoint(img, snap.FULL)
+        t1 = time.perf_counter()
+        s.close()
+        del ts
+        torch.cuda.empty_cache()
+        ts = fresh()  # restore goes into freshly allocated buffers
+        s = snap.Set(chunk_bytes=UNIT, ring_bytes=4 * GiB)
+        for t in ts:
+            s.register(t)
+        s.prepare(layout=True, ring=True)  # one-time setup outside the timed restore
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        s.restore(img, used)
+        t3 = time.perf_counter()
+        if timed:
+            ck.append(t1 - t0)
+            rs.append(t3 - t2)
+    clk = clocks.stop()
+    # parity on the sampled chunks: image bytes, image hashes, restored bytes
+    hdr = 64
+    ok = True
+    from struct import unpack_from
+    off = hdr
+    rec = []
+    for n in sizes:
+        k_n = (n + UNIT - 1) // UNIT
+        bk, nk, dk, _ = unpack_from("<QQQQ", m, off)
+        rec.append((off, dk))
+        off = (dk + n + 4095) // 4096 * 4096
+    for k, i, lo, hi, data in samples:
+        roff, dk = rec[k]
+        ok &= bytes(img[dk + lo: dk + hi]) == data.tobytes()
+        ok &= unpack_from("<I", m, roff + 32 + 4 * i)[0] == oracle.crc32c(data)
+        ok &= bool(np.array_equal(ts[k][lo:hi].cpu().numpy(), data))
+    mism = s.verify(img, used)
+    ckpt_gbs = B / statistics.median(ck) / 1e9
+    rest_gbs = B / statistics.median(rs) / 1e9
+    ms = (statistics.median(ck) + statistics.median(rs)) * 1e3
+    print(json.dumps(_line(args, world, 2 * B / (ms * 1e-3) / 1e9, ms,
+                           {"workload": "Llama-7B-shaped training state, 1,196 allocations, 115,812,655,104 B, "
+                                        "64 KiB chunks", "image": "pageable host memory via a 4 GiB pinned ring",
+                            "step": "full checkpoint + restore into freshly allocated device buffers",
+                            "l2": "115.8 GB state, larger than L2"},
+                           {"checkpoint_gbs": ckpt_gbs, "restore_gbs": rest_gbs,
+                            "roofline": {"bound": "host_link", "kernel": "ring checkpoint (gather + host copy)",
+                                         "achieved": ckpt_gbs, "peak": peaks["d2h"], "unit": "GB/s",
+                                         "frac": ckpt_gbs / peaks["d2h"]},
+                            "roofline_restore": {"bound": "host_link", "achieved": rest_gbs, "peak": peaks["h2d"],
+                                                 "unit": "GB/s", "frac": rest_gbs / peaks["h2d"]},
+                            "parity": {"sampled_chunks": len(samples), "sampled_bytes_hashes_restores_equal": bool(ok),
+                                       "verify_mismatches": mism},
+                            "image_populate_s": populate_s, "clocks": clk,
+                            "e2e": {"value": 2 * B / (ms * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": B,
+                                    "d2h_bytes_per_step": used}})))
+
+
+def run_serving(args, rank, world, local, pg):
+    """32 tenants (8-64 allocations log-uniform [1 MiB, 2 GiB], <= 4 GiB
+    each), Poisson arrivals at 20/s of full / incremental (5 % dirty) /
+    restore requests, budgets 64 GB pinned and 150 GB HBM; p50/p99 latency
+    and GB/s, against serial plain full copies of the same arrivals."""
+    import mmap
+    import threading
+    import torch
+    import paper_2502_16631_b300 as snap
+    tenants = workloads.config5_tenants(args.seed)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(args.seed)
+    T = []
+    for sizes in tenants:
+        ts = [torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g) for n in sizes]
+        s = snap.Set(chunk_bytes=UNIT)
+        for t in ts:
+            s.register(t)
+        nf = s.image_bytes(snap.FULL)
+        npb = min(s.image_bytes(snap.INCREMENTAL), nf // 8 + 64 * MiB)  # 5 % dirty fits easily
+        flags = mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS | getattr(mmap, "MAP_POPULATE", 0)
+        full = np.frombuffer(mmap.mmap(-1, nf, flags=flags), dtype=np.uint8)
+        patch = np.frombuffer(mmap.mmap(-1, npb, flags=flags), dtype=np.uint8)
+        nunits = sum((n + UNIT - 1) // UNIT for n in sizes)
+        T.append({"set": s, "ts": ts, "full": full, "patch": patch, "bytes": sum(sizes), "units": nunits,
+                  "has_image": False})
+    torch.cuda.synchronize()
+    # arrivals
+    r = workloads.Rng(args.seed ^ 0xA77)
+    t, reqs = 0.0, []
+    legal = [{"full"} for _ in T]
+    for i in range(args.arrivals):
+        t += -np.log(1.0 - r.uniform()) / args.rate
+        k = r.randint(0, len(T) - 1)
+        kinds = sorted(legal[k])
+        kind = kinds[r.randint(0, len(kinds) - 1)]
+        reqs.append((t, k, kind))
+        legal[k] |= {"incremental", "restore"}
+
+    def mutate(tk, seed):
+        """5 % of each allocation's whole 64 KiB units, every byte changed."""
+        gg = torch.Generator(device="cuda")
+        gg.manual_seed(seed)
+        for x in tk["ts"]:
+            n = x.numel() // UNIT
+            if n == 0:
+                continue
+            idx = torch.nonzero(torch.rand(n, generator=gg, device="cuda") < 0.05).flatten()
+            if idx.numel():
+                v = x[: n * UNIT].view(n, UNIT)
+                v[idx] ^= 0x5A
+        torch.cuda.synchronize()
+
+    sv = snap.Server(pinned_budget=64 * 10 ** 9, hbm_budget=150 * 10 ** 9, chunk_bytes=UNIT)
+    lat = [None] * len(reqs)
+    moved = [0] * len(reqs)
+    status = [0] * len(reqs)
+    per_tenant = [[] for _ in T]
+    for i, (ta, k, kind) in enumerate(reqs):
+        per_tenant[k].append(i)
+    start = time.perf_counter() + 0.5
+    lock = threading.Lock()
+
+    def tenant_loop(k):
+        tk = T[k]
+        torch.cuda.set_device(local)
+        for i in per_tenant[k]:
+            ta, _, kind = reqs[i]
+            # the tenant's own work between its requests (before the arrival)
+            if kind == "incremental":
+                mutate(tk, 7 * i + 1)
+                rk, buf = snap.REQ_INCREMENTAL, tk["patch"]
+            elif kind == "restore":
+                for x in tk["ts"]:
+                    x.fill_(0x33)  # scribble: the restore must bring the image back
+                torch.cuda.synchronize()
+                rk, buf = snap.REQ_RESTORE, tk["full"]
+            else:
+                rk, buf = snap.REQ_FULL, tk["full"]
+            delay = start + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ticket = sv.submit(tk["set"], rk, buf)
+            rc, st_, stats = sv.wait(ticket, 600000)
+            done = time.perf_counter()
+            with lock:
+                lat[i] = (done - (start + ta)) * 1e3
+                status[i] = st_
+                moved[i] = tk["bytes"]
+
+    th = [threading.Thread(target=tenant_loop, args=(k,)) for k in range(len(T))]
+    t0 = time.perf_counter()
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    wall = time.perf_counter() - max(t0, start)
+    sv.close()
+    good = [l for l, s_ in zip(lat, status) if s_ == 0 and l is not None]
+    gbs = sum(m_ for m_, s_ in zip(moved, status) if s_ == 0) / wall / 1e9
+    # serial plain full copies of the same arrivals (FIFO single server; each
+    # request's service time measured by running it, start = max(arrival,
+    # previous end)); the first 240 arrivals
+    nb = min(len(reqs), 240)
+    end, plain_lat = 0.0, []
+    for i in range(nb):
+        ta, k, kind = reqs[i]
+        tk = T[k]
+        t1 = time.perf_counter()
+        if kind == "restore":
+            tk["set"].plain_restore(tk["full"])
+        else:
+            tk["set"].plain_checkpoint(tk["full"])
+        svc = time.perf_counter() - t1
+        begin = max(ta, end)
+        end = begin + svc
+        plain_lat.append((end - ta) * 1e3)
+    ours_prefix = sorted(lat[:nb])
+    out = _line(args, world, gbs, wall * 1e3 / len(reqs),
+                {"workload": "serving: 32 tenants (8-64 allocations log-uniform [1 MiB, 2 GiB], <= 4 GiB each, "
+                             "%.1f GiB total), Poisson %.0f req/s, %d arrivals, full/incremental(5%%)/restore"
+                             % (sum(tk["bytes"] for tk in T) / GiB, args.rate, len(reqs)),
+                 "budgets": {"pinned": "64 GB", "hbm": "150 GB"}, "image": "pageable host memory"},
+                {"latency_ms": {"p50": float(np.percentile(good, 50)), "p99": float(np.percentile(good, 99)),
+                                "max": float(max(good)), "completed": len(good), "failed": len(reqs) - len(good)},
+                 "plain_serial_first_%d" % nb: {"p50": float(np.percentile(plain_lat, 50)),
+                                                "p99": float(np.percentile(plain_lat, 99)),
+                                                "ours_p50": float(np.percentile(ours_prefix, 50)),
+                                                "ours_p99": float(np.percentile(ours_prefix, 99))},
+                 "kinds": {k_: sum(1 for _, _, kk in reqs if kk == k_) for k_ in ("full", "incremental", "restore")}})
+    print(json.dumps(out))
+
+
 def _first_n(sizes, cap):
     tot, n = 0, 0
     for x in sizes:
@@ -482,8 +897,11 @@ def main():
     rank, world, local, pg = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
-    else:
+    elif args.workload == "gpt2":
         run_snap(args, rank, world, local, pg)
+    else:
+        {"random64m": run_random64m, "incr20g": run_incr20g, "llama7b": run_llama7b,
+         "serving": run_serving}[args.workload](args, rank, world, local, pg)
     if pg is not None:
         pg.destroy_process_group()
 

@@ -118,6 +118,15 @@ SNAP_API int snap_set_destroy(snap_set s);
  * an error (EINVAL, EBUSY). */
 SNAP_API int snap_register(snap_set s, void *dptr, uint64_t bytes);
 
+/* Do the set's one-time setup now instead of inside the first call: build
+ * its device tables (what & SNAP_PREPARE_LAYOUT) and allocate its pinned
+ * ring for pageable images (what & SNAP_PREPARE_RING).  Call it outside
+ * stream capture and outside latency-critical regions.  Errors: EINVAL,
+ * EBUSY, ENOMEM, ECUDA. */
+#define SNAP_PREPARE_LAYOUT 1
+#define SNAP_PREPARE_RING 2
+SNAP_API int snap_set_prepare(snap_set s, int what);
+
 /* Bytes a host image needs: exact for SNAP_FULL; an upper bound for
  * SNAP_INCREMENTAL (the patch size depends on how many chunks are dirty). */
 SNAP_API int snap_image_bytes(snap_set s, int mode, uint64_t *out);

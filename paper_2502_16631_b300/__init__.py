@@ -31,7 +31,7 @@ REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 
 # Every entry point declared in include/snap.h.
 EXPORTS = (
-    "snap_set_create", "snap_set_destroy", "snap_register", "snap_image_bytes",
+    "snap_set_create", "snap_set_destroy", "snap_set_prepare", "snap_register", "snap_image_bytes",
     "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_restore", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
@@ -87,6 +87,7 @@ def _lib():
         sig = {
             "snap_set_create": [P(vp), P(Opts)],
             "snap_set_destroy": [vp],
+            "snap_set_prepare": [vp, i32],
             "snap_register": [vp, vp, u64],
             "snap_image_bytes": [vp, i32, P(u64)],
             "snap_host_alloc": [u64, P(vp)],
@@ -208,6 +209,10 @@ class Set:
         if not isinstance(t, int):
             self.tensors.append(t)
         return _check(_lib().snap_register(self.h, _addr(t), nbytes), "snap_register")
+
+    def prepare(self, layout: bool = True, ring: bool = False) -> None:
+        """One-time setup now (device tables, pinned ring), not in the first call."""
+        _check(_lib().snap_set_prepare(self.h, (1 if layout else 0) | (2 if ring else 0)), "snap_set_prepare")
 
     def image_bytes(self, mode: int = FULL) -> int:
         v = ctypes.c_uint64()

@@ -57,7 +57,7 @@ void ring_free(snap_set_s *s)
     s->ring = nullptr;
 }
 
-static int ring_get(snap_set_s *s, Ring **out)
+int ring_get(snap_set_s *s, Ring **out)
 {
     if (s->ring) {
         *out = s->ring;

@@ -510,6 +510,20 @@ int snap_register(snap_set s, void *dptr, uint64_t bytes)
     return (int)(s->allocs.size() - 1);
 }
 
+int snap_set_prepare(snap_set s, int what)
+{
+    if (!s || (what & ~(SNAP_PREPARE_LAYOUT | SNAP_PREPARE_RING))) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    int rc = build_layout(s);
+    if (rc == SNAP_OK && (what & SNAP_PREPARE_RING)) {
+        Ring *r = nullptr;
+        rc = ring_get(s, &r);
+    }
+    return rc;
+}
+
 int snap_image_bytes(snap_set s, int mode, uint64_t *out)
 {
     if (!s || !out) return SNAP_EINVAL;

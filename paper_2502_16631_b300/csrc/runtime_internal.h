@@ -113,6 +113,7 @@ int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint6
 int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const ImageHeader &h, double t0, double tq,
                  double deadline);
 void ring_free(snap_set_s *s);
+int ring_get(snap_set_s *s, Ring **out);  // allocate the ring on first use
 
 // A window: global chunks [c0, c1) = packed-state bytes [b0, b1).
 struct Window {

@@ -273,6 +273,7 @@ def test_ring_pageable_images(C, ring):
     sizes = [8 * C + 100, 3 * C, 1, 0, 200000, C + 1, 70 * C]
     ts, hs = device_state(sizes, seed=41)
     s = make_set(ts, C, ring_bytes=ring)
+    s.prepare(layout=True, ring=True)
     full = np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8)  # pageable
     used = s.checkpoint(full, snap.FULL)
     assert np.array_equal(full[:used], oracle.write_full(hs, C, 0)[1])
