@@ -189,19 +189,38 @@ struct WarpCtx {
     uint32_t mbar;         // shared address of its first mbarrier
     uint32_t issued;       // stages issued so far (per warp, across chunks)
     uint32_t consumed;     // stages consumed so far
+    uint32_t ib, cb, cpar; // next buffer to issue / to consume, its phase parity
     int stages, piece, lane, chains;
     uint32_t lb;           // shared address of this lane's table column
     uint32_t stage_bytes;  // 32 * chains * (piece + 16)
 };
 
-__device__ __forceinline__ uint32_t buf_of(const WarpCtx &w, uint32_t g) { return g % (uint32_t)w.stages; }
-__device__ __forceinline__ uint32_t par_of(const WarpCtx &w, uint32_t g) { return (g / (uint32_t)w.stages) & 1u; }
+// The stage ring is walked with incremental counters (no division by the
+// runtime stage count): issue takes buffer ib; the next stage to consume is
+// buffer cb, whose mbarrier phase parity is cpar.
+__device__ __forceinline__ uint32_t issue_advance(WarpCtx &w)
+{
+    const uint32_t b = w.ib;
+    w.ib = (b + 1u == (uint32_t)w.stages) ? 0u : b + 1u;
+    ++w.issued;
+    return b;
+}
+__device__ __forceinline__ void cons_advance(WarpCtx &w)
+{
+    if (++w.cb == (uint32_t)w.stages) {
+        w.cb = 0u;
+        w.cpar ^= 1u;
+    }
+    ++w.consumed;
+}
 
 // Wait (bounded) for every issued, unconsumed stage: used when giving up.
 __device__ void drain(WarpCtx &w)
 {
-    for (uint32_t g = w.consumed; g < w.issued; ++g) (void)mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g));
-    w.consumed = w.issued;
+    while (w.consumed < w.issued) {
+        (void)mbar_wait(w.mbar + 8 * w.cb, w.cpar);
+        cons_advance(w);
+    }
 }
 
 // ------------------------------------------- segmented hash (HBM-bound path)
@@ -211,9 +230,9 @@ __device__ void drain(WarpCtx &w)
 // cp.async instruction of the warp moves four whole 128-byte lines.
 __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t s, uint32_t k)
 {
-    const uint32_t g = w.issued++;
+    const uint32_t buf = issue_advance(w);
     const uint32_t P = (uint32_t)w.piece;
-    uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+    uint8_t *sb = w.stage + buf * w.stage_bytes;
     const uint32_t sbs = smem_addr(sb);
     const uint32_t bpp = P >> 4;  // 16-byte blocks per piece
     for (uint32_t m = 0; m < bpp; ++m) {
@@ -226,7 +245,7 @@ __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32
         if (phi > L) phi = L;
         if (plo + 16u * b + 16u <= phi) cp_async16(sbs + j * (P + 16u) + 16u * b, src + plo + 16u * b);
     }
-    cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+    cp_async_arrive(w.mbar + 8 * buf);
 }
 
 // Full chunk (L == C, C/32 a multiple of P): the copy plan of every stage is
@@ -248,19 +267,19 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
     uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
 
     auto issue = [&](uint32_t k) {
-        const uint32_t g = w.issued++;
-        const uint32_t sbs = stage0 + buf_of(w, g) * w.stage_bytes;
+        const uint32_t buf = issue_advance(w);
+        const uint32_t sbs = stage0 + buf * w.stage_bytes;
 #pragma unroll
         for (uint32_t m = 0; m < BPP; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
-        cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+        cp_async_arrive(w.mbar + 8 * buf);
     };
     const uint32_t pre = nst < S ? nst : S;
     for (uint32_t k = 0; k < pre; ++k) issue(k);
     for (uint32_t k = 0; k < nst; ++k) {
-        const uint32_t g = w.consumed;
-        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
-        w.consumed++;
-        const uint32_t rd = stage0 + buf_of(w, g) * w.stage_bytes + lane * (P + 16u);
+        const uint32_t buf = w.cb;
+        if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
+        cons_advance(w);
+        const uint32_t rd = stage0 + buf * w.stage_bytes + lane * (P + 16u);
 #pragma unroll
         for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * b), w.lb);
         __syncwarp();
@@ -291,19 +310,19 @@ __device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, con
     uint32_t ca = lane == 0 ? 0xFFFFFFFFu : 0u, cb = 0u;
 
     auto issue = [&](uint32_t k) {
-        const uint32_t g = w.issued++;
-        const uint32_t sbs = stage0 + buf_of(w, g) * w.stage_bytes;
+        const uint32_t buf = issue_advance(w);
+        const uint32_t sbs = stage0 + buf * w.stage_bytes;
 #pragma unroll
         for (uint32_t m = 0; m < NI; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
-        cp_async_arrive(w.mbar + 8 * buf_of(w, g));
+        cp_async_arrive(w.mbar + 8 * buf);
     };
     const uint32_t pre = nst < S ? nst : S;
     for (uint32_t k = 0; k < pre; ++k) issue(k);
     for (uint32_t k = 0; k < nst; ++k) {
-        const uint32_t g = w.consumed;
-        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
-        w.consumed++;
-        const uint32_t ra = stage0 + buf_of(w, g) * w.stage_bytes + lane * (P + 16u);
+        const uint32_t buf = w.cb;
+        if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
+        cons_advance(w);
+        const uint32_t ra = stage0 + buf * w.stage_bytes + lane * (P + 16u);
         const uint32_t rb = ra + 32u * (P + 16u);
 #pragma unroll
         for (uint32_t b = 0; b < BPP; ++b) {
@@ -354,10 +373,10 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
     const uint32_t pre = nst < (uint32_t)w.stages ? nst : (uint32_t)w.stages;
     for (uint32_t k = 0; k < pre; ++k) seg_issue(w, src, L, s, k);
     for (uint32_t k = 0; k < nst; ++k) {
-        const uint32_t g = w.consumed;
-        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
-        w.consumed++;
-        const uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+        const uint32_t buf = w.cb;
+        if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
+        cons_advance(w);
+        const uint8_t *sb = w.stage + buf * w.stage_bytes;
         const uint32_t plo = lo + k * P;
         if (plo < hi) {
             const uint32_t phi = plo + P < hi ? plo + P : hi;
@@ -394,15 +413,15 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
 // the warp stores the stage to the host as contiguous 512-byte rows.
 __device__ __forceinline__ void int_issue(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t k)
 {
-    const uint32_t g = w.issued++;
+    const uint32_t buf = issue_advance(w);
     const uint32_t SB = 32u * (uint32_t)w.piece;
-    const uint32_t mb = w.mbar + 8 * buf_of(w, g);
+    const uint32_t mb = w.mbar + 8 * buf;
     if (w.lane == 0) {
         const uint32_t lo = k * SB;
         const uint32_t slen = (L - lo) < SB ? (L - lo) : SB;
         const uint32_t n16 = slen & ~15u;
         mbar_arrive_tx(mb, n16);
-        if (n16) tma_load_1d(smem_addr(w.stage + buf_of(w, g) * w.stage_bytes), src + lo, n16, mb);
+        if (n16) tma_load_1d(smem_addr(w.stage + buf * w.stage_bytes), src + lo, n16, mb);
     } else {
         mbar_arrive(mb);
     }
@@ -424,10 +443,10 @@ __device__ bool gather_chunk_int(WarpCtx &w, const uint8_t *src, uint32_t L, uin
     fence_proxy_async();
     for (uint32_t k = 0; k < pre; ++k) int_issue(w, src, L, k);
     for (uint32_t k = 0; k < nst; ++k) {
-        const uint32_t g = w.consumed;
-        if (!mbar_wait(w.mbar + 8 * buf_of(w, g), par_of(w, g))) return false;
-        w.consumed++;
-        const uint8_t *sb = w.stage + buf_of(w, g) * w.stage_bytes;
+        const uint32_t buf = w.cb;
+        if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
+        cons_advance(w);
+        const uint8_t *sb = w.stage + buf * w.stage_bytes;
         const uint32_t slo = k * SB;
         const uint32_t slen = (L - slo) < SB ? (L - slo) : SB;
         const uint32_t n16 = slen & ~15u;
@@ -505,7 +524,11 @@ __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, u
     return lo;
 }
 
-__global__ void __launch_bounds__(kMaxWarps * 32, 1)
+// HASH_ONLY instantiation: only OP_HASH / OP_VERIFY jobs, up to 32 warps per
+// CTA (1024 threads, so at most 64 registers a thread) to keep more lookup
+// chains in flight; the general one serves every op with up to 16 warps.
+template <bool HASH_ONLY>
+__global__ void __launch_bounds__(HASH_ONLY ? kMaxHashWarps * 32 : kMaxWarps * 32, 1)
 snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor, const CombineConsts cc,
            int stages, int piece, int chains, Result *kres)
 {
@@ -546,6 +569,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
     w.stage = stage_all + (size_t)warp * stages * stage_bytes;
     w.mbar = smem_addr(&mbars[warp * stages]);
     w.issued = w.consumed = 0;
+    w.ib = w.cb = w.cpar = 0;
     w.stages = stages;
     w.piece = piece;
     w.chains = chains;
@@ -605,6 +629,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
             }
             break;
         case OP_GATHER:
+            if (HASH_ONLY) {
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+                break;
+            }
             ok = gather_chunk_int(w, dsrc, L, (uint32_t)C, true, host_data, cc, h);
             if (ok) {
                 if (lane == 0) {
@@ -618,6 +646,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
             }
             break;
         case OP_GATHER_DIRTY: {
+            if (HASH_ONLY) {
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+                break;
+            }
             if (jb.cap_exceeded && *reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) break;
             // IMAGE: the chunk's slot in the patch (dirty rank window_off + tt);
             // PACKED: slot tt of a ring window of C-byte slots
@@ -629,6 +661,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
             break;
         }
         case OP_SCATTER:
+            if (HASH_ONLY) {
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+                break;
+            }
             scatter_chunk(host_data, reinterpret_cast<uint8_t *>(ad.ptr) + off, L, lane);
             break;
         default:
@@ -646,12 +682,17 @@ cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cu
                          const TileShape &sh, Result *kres, cudaStream_t st)
 {
     const size_t smem = tile_smem_bytes(sh);
-    if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxWarps || n_jobs < 1 || n_jobs > kMaxJobs)
+    // more than kMaxWarps warps selects the hash/verify-only kernel
+    if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxHashWarps || n_jobs < 1 || n_jobs > kMaxJobs)
         return cudaErrorInvalidValue;
     if (sh.chains < 1 || sh.chains > 2 || sh.stages < 1 || sh.piece < 32 || sh.piece > 256 || (sh.piece & 15))
         return cudaErrorInvalidValue;
-    snap_tiles<<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece, sh.chains,
-                                                     kres);
+    if (sh.warps > kMaxWarps)
+        snap_tiles<true><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece,
+                                                               sh.chains, kres);
+    else
+        snap_tiles<false><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece,
+                                                                sh.chains, kres);
     return cudaGetLastError();
 }
 
@@ -659,7 +700,10 @@ cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cu
 // device, outside any stream capture.
 cudaError_t init_tile_kernel()
 {
-    return cudaFuncSetAttribute(snap_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(snap_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(snap_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    return e;
 }
 
 CombineConsts make_combine_consts(uint64_t C, int piece)

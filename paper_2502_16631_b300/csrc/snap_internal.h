@@ -74,7 +74,8 @@ struct Job {
 };
 
 constexpr int kMaxJobs = 64;
-constexpr int kMaxWarps = 16;
+constexpr int kMaxWarps = 16;      // general tile kernel
+constexpr int kMaxHashWarps = 32;  // hash/verify-only tile kernel
 
 // Launch shape of the persistent tile kernel.
 struct TileShape {
