@@ -529,9 +529,14 @@ __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, u
 // chains in flight; the general one serves every op with up to 16 warps.
 template <bool HASH_ONLY>
 __global__ void __launch_bounds__(HASH_ONLY ? kMaxHashWarps * 32 : kMaxWarps * 32, 1)
-snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor, const CombineConsts cc,
-           int stages, int piece, int chains, Result *kres)
+snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long long *cursor,
+           unsigned long long *cursor_b, const CombineConsts cc, int stages, int piece, int chains, Result *kres)
 {
+    // Jobs [0, n_jobs_a) form group A (device -> host work), jobs
+    // [n_jobs_a, n_jobs) group B (host -> device work); each group has its own
+    // tile cursor, even warps start on A and odd warps on B, and a warp
+    // whose group runs dry switches to the other, so a launch that mixes
+    // checkpoints and restores drives both link directions at once.
     extern __shared__ __align__(1024) uint8_t smem[];
     uint32_t *tables = reinterpret_cast<uint32_t *>(smem);
     const int warps = blockDim.x >> 5;
@@ -564,6 +569,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
     fence_mbar_init();
     __syncthreads();
     const unsigned long long total = prefix[n_jobs];
+    const unsigned long long tot_a = cursor_b ? prefix[n_jobs_a] : total;
+    const unsigned long long tot_b = total - tot_a;
+    bool done_a = tot_a == 0, done_b = tot_b == 0;
+    int grp = (tot_b != 0 && (warp & 1)) ? 1 : 0;
 
     WarpCtx w;
     w.stage = stage_all + (size_t)warp * stages * stage_bytes;
@@ -578,10 +587,17 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
     w.stage_bytes = stage_bytes;
 
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(cursor, 1ull);
-        t = __shfl_sync(0xFFFFFFFFu, t, 0);
-        if (t >= total) break;
+        if (done_a && done_b) break;
+        if (grp == 0 && done_a) grp = 1;
+        if (grp == 1 && done_b) grp = 0;
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(grp ? cursor_b : cursor, 1ull);
+        v = __shfl_sync(0xFFFFFFFFu, v, 0);
+        if (v >= (grp ? tot_b : tot_a)) {
+            if (grp) done_b = true; else done_a = true;
+            continue;
+        }
+        const unsigned long long t = grp ? tot_a + v : v;
         // another warp gave up: stop (lane 0 reads, the warp follows it)
         unsigned long long err = lane == 0 ? *reinterpret_cast<volatile unsigned long long *>(&kres->err) : 0ull;
         if (__shfl_sync(0xFFFFFFFFu, err, 0)) break;
@@ -678,22 +694,30 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, unsigned long long *cursor,
     }
 }
 
-cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor, const CombineConsts &cc,
-                         const TileShape &sh, Result *kres, cudaStream_t st)
+cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigned long long *cursor_a,
+                          unsigned long long *cursor_b, const CombineConsts &cc, const TileShape &sh, Result *kres,
+                          cudaStream_t st)
 {
     const size_t smem = tile_smem_bytes(sh);
     // more than kMaxWarps warps selects the hash/verify-only kernel
     if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxHashWarps || n_jobs < 1 || n_jobs > kMaxJobs)
         return cudaErrorInvalidValue;
+    if (n_jobs_a < 0 || n_jobs_a > n_jobs || (n_jobs_a < n_jobs && !cursor_b)) return cudaErrorInvalidValue;
     if (sh.chains < 1 || sh.chains > 2 || sh.stages < 1 || sh.piece < 32 || sh.piece > 256 || (sh.piece & 15))
         return cudaErrorInvalidValue;
     if (sh.warps > kMaxWarps)
-        snap_tiles<true><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece,
-                                                               sh.chains, kres);
+        snap_tiles<true><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
+                                                               sh.stages, sh.piece, sh.chains, kres);
     else
-        snap_tiles<false><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, cursor, cc, sh.stages, sh.piece,
-                                                                sh.chains, kres);
+        snap_tiles<false><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
+                                                                sh.stages, sh.piece, sh.chains, kres);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor, const CombineConsts &cc,
+                         const TileShape &sh, Result *kres, cudaStream_t st)
+{
+    return launch_tiles2(jobs_dev, n_jobs, n_jobs, cursor, nullptr, cc, sh, kres, st);
 }
 
 // Opt the kernel into the full shared-memory carve-out; call once per

@@ -15,6 +15,7 @@
 #include "snap_format.h"
 #include "runtime_internal.h"
 #include "host_pool.h"
+#include "host_copy.h"
 
 #include <algorithm>
 #include <atomic>
@@ -168,8 +169,8 @@ void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8
         if (x1 <= x0) continue;
         uint8_t *img = image + a.data_off + (x0 - a.state_off);
         uint8_t *sl = slot + (x0 - w.b0);
-        if (to_image) std::memcpy(img, sl, x1 - x0);
-        else std::memcpy(sl, img, x1 - x0);
+        if (to_image) stream_copy(img, sl, x1 - x0);
+        else stream_copy(sl, img, x1 - x0);
     }
 }
 
@@ -413,7 +414,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
                     const AllocDesc &a = s->desc[k];
                     const uint64_t i = c - a.chunk0;
                     const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
-                    std::memcpy(image + pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
+                    stream_copy(image + pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
                 }
             }
             pg.done(w);

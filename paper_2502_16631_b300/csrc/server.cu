@@ -21,9 +21,11 @@
 #include "snap_format.h"
 #include "runtime_internal.h"
 #include "host_pool.h"
+#include "host_copy.h"
 
 #include <algorithm>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -36,6 +38,7 @@ namespace snapk {
 namespace {
 
 constexpr int kRounds = 2;
+constexpr size_t kMinBatch = 8;  // windows a round waits for while another runs
 constexpr uint64_t kStagingCap = 2ull << 30;  // pinned staging charged per request
 
 static inline uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
@@ -83,6 +86,7 @@ struct Round {
     cudaEvent_t ev = nullptr;
     std::vector<std::pair<SReq *, size_t>> wins;
     bool busy = false;
+    double t_launch = 0;
 };
 
 }  // namespace
@@ -113,6 +117,10 @@ struct snap_server_s {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread sched;
+    // counters, printed at destroy when SNAP_LOG is set
+    uint64_t n_rounds = 0, n_windows = 0, host_bytes = 0;
+    double gpu_busy_ms = 0, host_copy_ms = 0, t_first = 0, t_last = 0;
+    std::mutex stat_mu;
 };
 
 namespace snapk {
@@ -263,7 +271,7 @@ void drain_dirty(const SReq *r, const SWin &w, const uint8_t *slot)
         const AllocDesc &a = s->desc[k];
         const uint64_t i = c - a.chunk0;
         const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
-        std::memcpy(r->image + r->pdat[k] + (q - r->dst[k]) * s->C, slot + (q - w.c0) * s->C, upg(L));
+        stream_copy(r->image + r->pdat[k] + (q - r->dst[k]) * s->C, slot + (q - w.c0) * s->C, upg(L));
     }
 }
 
@@ -376,7 +384,13 @@ void start_fill(snap_server_s *sv, SReq *r, size_t wi)
     for (uint64_t p = 0; p < np; ++p) {
         const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
         sv->workers->push([sv, r, wi, x, slot, p0, p1] {
+            const double c0 = now_ms();
             copy_window_part(r->set, x, slot, r->image, p0, p1, false);
+            {
+                std::lock_guard<std::mutex> g(sv->stat_mu);
+                sv->host_copy_ms += now_ms() - c0;
+                sv->host_bytes += p1 - p0;
+            }
             std::lock_guard<std::mutex> lk(sv->mu);
             SWin &ww = r->wins[wi];
             if (--ww.parts == 0) ww.state = W_READY;
@@ -414,7 +428,13 @@ void start_drain(snap_server_s *sv, SReq *r, size_t wi)
     for (uint64_t p = 0; p < np; ++p) {
         const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
         sv->workers->push([sv, r, wi, x, slot, p0, p1] {
+            const double c0 = now_ms();
             copy_window_part(r->set, x, slot, r->image, p0, p1, true);
+            {
+                std::lock_guard<std::mutex> g(sv->stat_mu);
+                sv->host_copy_ms += now_ms() - c0;
+                sv->host_bytes += p1 - p0;
+            }
             std::lock_guard<std::mutex> lk(sv->mu);
             SWin &ww = r->wins[wi];
             if (--ww.parts == 0) {
@@ -425,6 +445,20 @@ void start_drain(snap_server_s *sv, SReq *r, size_t wi)
             sv->cv.notify_all();
         });
     }
+}
+
+// Windows that could join a round now.
+size_t count_ready(const snap_server_s *sv)
+{
+    size_t n = 0, need_slot = 0;
+    for (const SReq *r : sv->active) {
+        if (r->phase != P_WINDOWS && r->phase != P_HASH) continue;
+        for (const SWin &w : r->wins) {
+            if (w.state == W_READY) ++n;
+            else if (w.state == W_WAIT && w.op != OP_SCATTER) ++need_slot;
+        }
+    }
+    return n + std::min<size_t>(need_slot, sv->free_slots.size());
 }
 
 // Fill one round with ready windows, round-robin over the active requests.
@@ -460,6 +494,11 @@ bool build_round(snap_server_s *sv, Round &rd)
 
 cudaError_t launch_round(snap_server_s *sv, Round &rd)
 {
+    // device -> host (and hash) windows first, restores last: the kernel
+    // works on the two groups with separate cursors, both link directions
+    auto is_a = [](const std::pair<SReq *, size_t> &p) { return p.first->wins[p.second].op != OP_SCATTER; };
+    const auto mid = std::stable_partition(rd.wins.begin(), rd.wins.end(), is_a);
+    const int n_a = (int)(mid - rd.wins.begin());
     for (size_t q = 0; q < rd.wins.size(); ++q) {
         SReq *r = rd.wins[q].first;
         const SWin &w = r->wins[rd.wins[q].second];
@@ -483,13 +522,21 @@ cudaError_t launch_round(snap_server_s *sv, Round &rd)
     }
     std::memset(rd.h_res, 0, sizeof(Result));
     cudaError_t e = cudaMemcpyAsync(rd.d_jobs, rd.h_jobs, sizeof(Job) * rd.wins.size(), cudaMemcpyHostToDevice, sv->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(rd.d_cursor, 0, sizeof(unsigned long long), sv->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rd.d_cursor, 0, 2 * sizeof(unsigned long long), sv->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(rd.d_res, 0, sizeof(Result), sv->st);
     if (e == cudaSuccess)
-        e = launch_tiles(rd.d_jobs, (int)rd.wins.size(), rd.d_cursor, sv->cc, sv->shape, rd.d_res, sv->st);
+        e = launch_tiles2(rd.d_jobs, (int)rd.wins.size(), n_a, rd.d_cursor, rd.d_cursor + 1, sv->cc, sv->shape,
+                          rd.d_res, sv->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(rd.h_res, rd.d_res, sizeof(Result), cudaMemcpyDeviceToHost, sv->st);
     if (e == cudaSuccess) e = cudaEventRecord(rd.ev, sv->st);
     rd.busy = e == cudaSuccess;
+    if (rd.busy) {
+        const double t = now_ms();
+        rd.t_launch = t;
+        if (sv->t_first == 0) sv->t_first = t;
+        ++sv->n_rounds;
+        sv->n_windows += rd.wins.size();
+    }
     return e;
 }
 
@@ -560,6 +607,13 @@ void scheduler(snap_server_s *sv)
             const cudaError_t q = cudaEventQuery(rd.ev);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) rd.h_res->err |= 1;
+            {
+                // rounds finish in stream order: busy time is the union of
+                // [launch, completion] intervals
+                const double t = now_ms();
+                sv->gpu_busy_ms += t - std::max(rd.t_launch, sv->t_last);
+                sv->t_last = t;
+            }
             complete_round(sv, rd);
         }
         // hash passes done -> diff and dirty windows
@@ -593,6 +647,11 @@ void scheduler(snap_server_s *sv)
         // launch into free round buffers
         for (Round &rd : sv->rounds) {
             if (rd.busy) continue;
+            // while the GPU is busy, let windows accumulate so that a round
+            // batches several requests (and both link directions)
+            bool gpu_busy = false;
+            for (const Round &o : sv->rounds) gpu_busy |= o.busy;
+            if (gpu_busy && count_ready(sv) < kMinBatch) break;
             if (!build_round(sv, rd)) break;
             const cudaError_t e = launch_round(sv, rd);
             if (e != cudaSuccess) {
@@ -662,7 +721,7 @@ int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_bu
         Round &rd = sv->rounds[i];
         e = cudaMalloc((void **)&rd.d_jobs, sizeof(Job) * kMaxJobs);
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&rd.h_jobs, sizeof(Job) * kMaxJobs, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&rd.d_cursor, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&rd.d_cursor, 2 * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc((void **)&rd.d_res, sizeof(Result));
         if (e == cudaSuccess) e = cudaHostAlloc((void **)&rd.h_res, sizeof(Result), cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&rd.ev, cudaEventDisableTiming);
@@ -674,7 +733,9 @@ int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_bu
     }
     for (int i = 0; i < sv->nslots; ++i) sv->free_slots.push_back(i);
     const int hw = (int)std::thread::hardware_concurrency();
-    sv->workers = new Pool(std::max(2, std::min(12, hw > 2 ? hw - 2 : 2)));
+    int nw = std::max(2, std::min(12, hw > 2 ? hw - 2 : 2));
+    if (const char *w = std::getenv("SNAP_WORKERS")) nw = std::max(1, std::min(64, std::atoi(w)));
+    sv->workers = new Pool(nw);
     sv->sched = std::thread(scheduler, sv);
     *out = sv;
     return SNAP_OK;
@@ -691,6 +752,15 @@ int snap_server_destroy(snap_server sv)
         sv->cv.notify_all();
         sv->sched.join();  // the scheduler finishes admitted and queued requests first
     }
+    if (std::getenv("SNAP_LOG") && sv->n_rounds)
+        std::fprintf(stderr,
+                     "snap_server: %llu rounds, %.1f windows/round, GPU busy %.1f %% of %.1f s, host copies %.1f GB "
+                     "at %.1f GB/s per worker (%d workers), pool %d x %llu MiB\n",
+                     (unsigned long long)sv->n_rounds, (double)sv->n_windows / sv->n_rounds,
+                     100.0 * sv->gpu_busy_ms / std::max(1.0, sv->t_last - sv->t_first),
+                     (sv->t_last - sv->t_first) * 1e-3, sv->host_bytes * 1e-9,
+                     sv->host_bytes / std::max(1e-9, sv->host_copy_ms * 1e-3) * 1e-9, sv->workers->size(),
+                     sv->nslots, (unsigned long long)(sv->slot_bytes >> 20));
     delete sv->workers;
     cudaSetDevice(sv->device);
     if (sv->st) cudaStreamSynchronize(sv->st);
