@@ -174,16 +174,6 @@ void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8
     }
 }
 
-bool poll_event(cudaEvent_t e, double deadline)
-{
-    for (;;) {
-        const cudaError_t q = cudaEventQuery(e);
-        if (q == cudaSuccess) return true;
-        if (q != cudaErrorNotReady || now_ms() > deadline) return false;
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
-    }
-}
-
 static Job window_job(const snap_set_s *s, Ring *r, int slot, uint32_t op, const Window &w, uint32_t *hash_out)
 {
     Job j{};
@@ -217,6 +207,14 @@ uint64_t parts_for(uint64_t bytes, int threads)
 {
     const uint64_t p = std::max<uint64_t>(1, bytes / (8ull << 20));  // about 8 MiB per part
     return std::min<uint64_t>(p, (uint64_t)threads * 2);
+}
+
+// Kernels this call launched may still be running after an error: the next
+// call on the set waits for them (bounded) before it reuses the ring.
+static void mark_in_flight(snap_set_s *s)
+{
+    if (cudaEventRecord(s->ev[EV_END], s->st) == cudaSuccess) s->in_flight = true;
+    else cudaGetLastError();
 }
 
 // Wait for every queued worker task (bounded); used on every exit path so
@@ -263,7 +261,10 @@ static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, doubl
         for (uint64_t p = 0; p < np; ++p) {
             const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
             r->pool->push([&, w, slot, p0, p1] {
-                if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+                if (!pg.err) {
+                    const int q = wait_event(r->ev[slot], deadline);  // ETIMEDOUT or ECUDA
+                    if (q) pg.err = q;
+                }
                 if (!pg.err)
                     copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, image, p0, p1, true);
                 pg.done(w);
@@ -273,7 +274,10 @@ static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, doubl
     if (e != cudaSuccess && rc == SNAP_OK) rc = cuda_status(e);
     drain(pg);
     if (rc == SNAP_OK && pg.err) rc = pg.err;
-    if (rc) return rc;
+    if (rc) {
+        mark_in_flight(s);
+        return rc;
+    }
     // hashes and kernel flags
     if (s->n_chunks)
         e = cudaMemcpyAsync(s->h_hash_stage, s->d_hash[cur], s->n_chunks * 4, cudaMemcpyDeviceToHost, s->st);
@@ -403,7 +407,10 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
             pg.outstanding += 1;
         }
         r->pool->push([&, w, slot, r0, r1] {
-            if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+            if (!pg.err) {
+                const int q = wait_event(r->ev[slot], deadline);
+                if (q) pg.err = q;
+            }
             if (!pg.err) {
                 const uint8_t *sl = r->host + (uint64_t)slot * r->slot_bytes;
                 size_t k = 0;
@@ -422,7 +429,10 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
     }
     drain(pg);
     if (rc == SNAP_OK && pg.err) rc = pg.err;
-    if (rc) return rc;
+    if (rc) {
+        mark_in_flight(s);
+        return rc;
+    }
     e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda_status(e);
@@ -508,7 +518,10 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
                 if (w >= (size_t)r->slots && !pg.err) {
                     const size_t prev = w - r->slots;
                     if (!pg.wait(deadline, [&] { return pg.launched[prev] != 0; })) pg.err = SNAP_ETIMEDOUT;
-                    if (!pg.err && !poll_event(r->ev[slot], deadline)) pg.err = SNAP_ETIMEDOUT;
+                    if (!pg.err) {
+                        const int q = wait_event(r->ev[slot], deadline);
+                        if (q) pg.err = q;
+                    }
                 }
                 if (!pg.err)
                     copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, img, p0, p1, false);
@@ -544,7 +557,7 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
     }
     drain(pg);
     if (rc) {
-        cudaStreamSynchronize(s->st);
+        mark_in_flight(s);
         return rc;
     }
     e = cudaMemcpyAsync(s->h_res, &s->d_cb->res, sizeof(Result), cudaMemcpyDeviceToHost, s->st);

@@ -122,7 +122,6 @@ struct Window {
 std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes);
 void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0, uint64_t p1,
                       bool to_image);
-bool poll_event(cudaEvent_t e, double deadline);
 uint64_t parts_for(uint64_t bytes, int threads);
 
 // (Re)build a set's device layout after registrations (runtime.cu).
