@@ -80,6 +80,8 @@ typedef struct {
     uint32_t ctas_per_sm;  /* persistent CTAs per SM; 0 = tuned default */
     uint32_t stages;       /* staging buffers per warp; 0 = tuned default */
     uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB */
+    uint32_t async_ctas;   /* CTAs of the background part of snap_checkpoint_async;
+                              default a quarter of the SMs */
 } snap_opts;
 
 /* Per-call statistics (times in milliseconds; quiesce_ms and total_ms are
@@ -97,6 +99,9 @@ typedef struct {
     double copy_ms;          /* gather (checkpoint) or scatter (restore)  */
     double total_ms;         /* call entry to return                      */
     uint64_t kernel_launches; /* libsnap kernels the call ran on the GPU  */
+    double frozen_ms;        /* how long the caller was held: the whole call
+                                for synchronous calls; quiesce + cut for
+                                snap_checkpoint_async                     */
 } snap_stats;
 
 /* ------------------------------------------------------------------ sets */
@@ -125,6 +130,7 @@ SNAP_API int snap_register(snap_set s, void *dptr, uint64_t bytes);
  * EBUSY, ENOMEM, ECUDA. */
 #define SNAP_PREPARE_LAYOUT 1
 #define SNAP_PREPARE_RING 2
+#define SNAP_PREPARE_SHADOW 4  /* device shadow for snap_checkpoint_async */
 SNAP_API int snap_set_prepare(snap_set s, int what);
 
 /* Bytes a host image needs: exact for SNAP_FULL; an upper bound for
@@ -153,6 +159,25 @@ SNAP_API int snap_host_free(void *p);
  * the image size.  Errors: EINVAL (cap too small: nothing committed),
  * ENOBASE, ETIMEDOUT, EBUSY, ENOMEM, ECUDA. */
 SNAP_API int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used);
+
+/* Asynchronous checkpoint (the overlapped snapshotting Sec. 7 cites from
+ * CheckFreq/Nebula/Gemini): quiesce the caller's stream, copy every
+ * registered allocation device to device into a library-owned shadow
+ * buffer (the cut), and return; the caller may then modify its allocations
+ * freely.  Hashing, diffing and the transfer into host_image (pinned and
+ * mapped: snap_host_alloc memory) run from the shadow on a lowest-priority
+ * stream with opts.async_ctas CTAs, leaving the other SMs to the caller.
+ * The result is exactly what snap_checkpoint would have produced at the
+ * cut.  The set stays busy (EBUSY for other calls) until
+ * snap_checkpoint_wait.  The shadow (the packed size of the state) is
+ * allocated on first use, or by snap_set_prepare(SNAP_PREPARE_SHADOW).
+ * Errors as snap_checkpoint, plus EINVAL for a pageable image. */
+SNAP_API int snap_checkpoint_async(snap_set s, void *host_image, uint64_t cap, int mode);
+
+/* Wait up to timeout_ms for the pending asynchronous checkpoint; on
+ * completion write its header, commit and return its status (*used = image
+ * bytes).  ETIMEDOUT leaves it pending; EINVAL if none is pending. */
+SNAP_API int snap_checkpoint_wait(snap_set s, uint32_t timeout_ms, uint64_t *used);
 
 /* Restore a full image into the set's registered buffers (Sec. 3.1.1
  * "restore"; Sec. 6).  The image must describe the same allocation count and

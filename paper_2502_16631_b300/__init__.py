@@ -32,7 +32,8 @@ REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 # Every entry point declared in include/snap.h.
 EXPORTS = (
     "snap_set_create", "snap_set_destroy", "snap_set_prepare", "snap_register", "snap_image_bytes",
-    "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_restore", "snap_verify",
+    "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_checkpoint_async", "snap_checkpoint_wait",
+    "snap_restore", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
     "snap_autotune",
@@ -51,7 +52,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint64), ("timeout_ms", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("ctas_per_sm", ctypes.c_uint32), ("stages", ctypes.c_uint32),
-                ("ring_bytes", ctypes.c_uint64)]
+                ("ring_bytes", ctypes.c_uint64), ("async_ctas", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -60,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("mismatches", ctypes.c_uint64), ("generation", ctypes.c_uint64),
                 ("quiesce_ms", ctypes.c_double), ("hash_ms", ctypes.c_double),
                 ("diff_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64)]
+                ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
+                ("frozen_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +95,8 @@ def _lib():
             "snap_host_alloc": [u64, P(vp)],
             "snap_host_free": [vp],
             "snap_checkpoint": [vp, vp, u64, i32, P(u64)],
+            "snap_checkpoint_async": [vp, vp, u64, i32],
+            "snap_checkpoint_wait": [vp, u32, P(u64)],
             "snap_restore": [vp, u64, vp],
             "snap_verify": [vp, u64, vp, P(u64)],
             "snap_apply_patch": [vp, u64, vp, u64],
@@ -184,8 +188,9 @@ class Set:
     """A set of registered device allocations (snap_set)."""
 
     def __init__(self, chunk_bytes: int = 0, timeout_ms: int = 0, device: int = -1, stream=None,
-                 ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0):
-        o = Opts(chunk_bytes, timeout_ms, device, _stream_handle(stream), ctas_per_sm, stages, ring_bytes)
+                 ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0, async_ctas: int = 0):
+        o = Opts(chunk_bytes, timeout_ms, device, _stream_handle(stream), ctas_per_sm, stages, ring_bytes,
+                 async_ctas)
         h = ctypes.c_void_p()
         _check(_lib().snap_set_create(ctypes.byref(h), ctypes.byref(o)), "snap_set_create")
         self.h = h.value
@@ -210,9 +215,10 @@ class Set:
             self.tensors.append(t)
         return _check(_lib().snap_register(self.h, _addr(t), nbytes), "snap_register")
 
-    def prepare(self, layout: bool = True, ring: bool = False) -> None:
-        """One-time setup now (device tables, pinned ring), not in the first call."""
-        _check(_lib().snap_set_prepare(self.h, (1 if layout else 0) | (2 if ring else 0)), "snap_set_prepare")
+    def prepare(self, layout: bool = True, ring: bool = False, shadow: bool = False) -> None:
+        """One-time setup now (device tables, pinned ring, async shadow), not in the first call."""
+        what = (1 if layout else 0) | (2 if ring else 0) | (4 if shadow else 0)
+        _check(_lib().snap_set_prepare(self.h, what), "snap_set_prepare")
 
     def image_bytes(self, mode: int = FULL) -> int:
         v = ctypes.c_uint64()
@@ -229,6 +235,24 @@ class Set:
         used = ctypes.c_uint64()
         rc = _lib().snap_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
                                     ctypes.byref(used))
+        return rc, used.value
+
+    def checkpoint_async(self, image, mode: int = FULL, cap: int | None = None) -> None:
+        """Start an asynchronous checkpoint; returns once the cut is taken."""
+        _check(self.checkpoint_async_status(image, mode, cap), "snap_checkpoint_async")
+
+    def checkpoint_async_status(self, image, mode: int = FULL, cap: int | None = None) -> int:
+        return _lib().snap_checkpoint_async(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode)
+
+    def checkpoint_wait(self, timeout_ms: int = 60000) -> int:
+        """Finish the pending asynchronous checkpoint; returns the image bytes."""
+        rc, used = self.checkpoint_wait_status(timeout_ms)
+        _check(rc, "snap_checkpoint_wait")
+        return used
+
+    def checkpoint_wait_status(self, timeout_ms: int = 60000):
+        used = ctypes.c_uint64()
+        rc = _lib().snap_checkpoint_wait(self.h, timeout_ms, ctypes.byref(used))
         return rc, used.value
 
     def restore(self, image, nbytes: int | None = None) -> None:

@@ -24,6 +24,59 @@ cudaError_t launch_stamp(Result *res, int idx, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------- snapshot cut (shadow)
+// The cut of an asynchronous checkpoint: every chunk of every allocation is
+// copied device to device into the set's shadow buffer (packed layout,
+// allocation k at shadow + state_off_k), so the caller may resume writing
+// its allocations while the image is produced from the shadow.  Each warp
+// copies whole chunks with 16-byte loads and stores, 4 in flight per lane.
+__device__ __forceinline__ uint64_t find_alloc_chunk(const AllocDesc *a, uint64_t n, uint64_t chunk)
+{
+    uint64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid].chunk0 <= chunk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_shadow_copy(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C, uint64_t n_chunks,
+                              uint8_t *shadow)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < n_chunks; c += warps) {
+        const AllocDesc a = allocs[find_alloc_chunk(allocs, n_allocs, c)];
+        const uint64_t off = (c - a.chunk0) * C;
+        const uint64_t L = (a.bytes - off) < C ? (a.bytes - off) : C;
+        const uint4 *s = reinterpret_cast<const uint4 *>(a.ptr + off);
+        uint4 *d = reinterpret_cast<uint4 *>(shadow + a.state_off + off);
+        const uint64_t nb = L >> 4;
+        uint64_t q = lane;
+        for (; q + 96 < nb; q += 128) {
+            const uint4 v0 = s[q], v1 = s[q + 32], v2 = s[q + 64], v3 = s[q + 96];
+            d[q] = v0;
+            d[q + 32] = v1;
+            d[q + 64] = v2;
+            d[q + 96] = v3;
+        }
+        for (; q < nb; q += 32) d[q] = s[q];
+        const uint64_t rem = L & 15u;
+        if ((uint64_t)lane < rem) {
+            const uint8_t *sb = reinterpret_cast<const uint8_t *>(a.ptr + off);
+            shadow[a.state_off + off + (nb << 4) + lane] = sb[(nb << 4) + lane];
+        }
+    }
+}
+
+cudaError_t launch_shadow_copy(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, uint64_t n_chunks,
+                               uint8_t *shadow, int sms, cudaStream_t st)
+{
+    if (n_chunks == 0) return cudaSuccess;
+    k_shadow_copy<<<sms * 8, 256, 0, st>>>(allocs, n_allocs, C, n_chunks, shadow);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------ full image: record headers
 // Block k writes allocation k's 32-byte record {bytes, n, data_off, 0} and
 // zeroes the padding between its hash array and its data.  (The hashes, the

@@ -474,6 +474,7 @@ int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint6
     st.generation = gen;
     st.quiesce_ms = tq - t0;
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }
@@ -577,6 +578,7 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
     st.copy_ms = now_ms() - tc0;
     st.kernel_launches = W;
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }

@@ -181,6 +181,7 @@ static void free_device(snap_set_s *s)
     s->d_blockoff = nullptr;
     s->d_patch_rec = s->d_patch_data = s->d_dstart = nullptr;
     s->h_hash_stage = nullptr;
+    async_free_layout(s);
 }
 
 int build_layout(snap_set_s *s)
@@ -243,16 +244,10 @@ int build_layout(snap_set_s *s)
 }
 
 // ------------------------------------------------------------ call plumbing
-struct BusyGuard {
-    snap_set_s *s;
-    bool ok;
-    explicit BusyGuard(snap_set_s *s_) : s(s_) { ok = !s->busy.exchange(true); }
-    ~BusyGuard() { if (ok) s->busy.store(false); }
-};
 
 // A previous call that timed out may still be running on the library
 // stream; wait for it (bounded) before touching shared buffers again.
-static int settle(snap_set_s *s, double deadline)
+int settle(snap_set_s *s, double deadline)
 {
     if (!s->in_flight) return SNAP_OK;
     const int rc = wait_event(s->ev[EV_END], deadline);
@@ -262,7 +257,7 @@ static int settle(snap_set_s *s, double deadline)
 
 // Quiesce the caller's stream: every operation queued on it must finish
 // before the snapshot reads device memory (the lock action, Sec. 3.1.1).
-static int quiesce(snap_set_s *s, double deadline)
+int quiesce(snap_set_s *s, double deadline)
 {
     cudaError_t e = cudaEventRecord(s->ev_quiesce, s->user_stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -275,10 +270,12 @@ TileShape shape_for(const snap_set_s *s, int kind)
     return sh;
 }
 
-// Capture (once) and launch the graph for `kind`; parity selects which hash
-// table is "current".
-static int run_graph(snap_set_s *s, int kind, int parity, const std::function<cudaError_t(cudaStream_t)> &body)
+// The graph for `kind`, captured from `body` on first use; parity selects
+// which hash table is "current".
+int get_graph(snap_set_s *s, int kind, int parity, const std::function<cudaError_t(cudaStream_t)> &body,
+              GraphEntry **out)
 {
+    *out = nullptr;
     GraphEntry *g = nullptr;
     for (auto &x : s->graphs)
         if (x.kind == kind && x.parity == parity) g = &x;
@@ -310,6 +307,15 @@ static int run_graph(snap_set_s *s, int kind, int parity, const std::function<cu
         s->graphs.push_back(GraphEntry{kind, parity, exec, kernels});
         g = &s->graphs.back();
     }
+    *out = g;
+    return SNAP_OK;
+}
+
+static int run_graph(snap_set_s *s, int kind, int parity, const std::function<cudaError_t(cudaStream_t)> &body)
+{
+    GraphEntry *g = nullptr;
+    const int rc = get_graph(s, kind, parity, body, &g);
+    if (rc) return rc;
     s->call_kernels = g->kernels;
     return cuda_status(cudaGraphLaunch(g->exec, s->st));
 }
@@ -381,6 +387,110 @@ static int finish(snap_set_s *s, double deadline)
     }
     if (rc) return rc;
     if (s->h_res->err) return SNAP_ECUDA;
+    return SNAP_OK;
+}
+
+int async_ctas(const snap_set_s *s)
+{
+    const int c = s->opts.async_ctas ? (int)s->opts.async_ctas : s->sms / 4;
+    return std::max(1, std::min(c, s->sms));
+}
+
+// Fill the call block of a checkpoint into the mapped image `dimg` and get
+// (capturing it on first use) its graph: FULL = records + gather of every
+// chunk with its CRC; INCREMENTAL = hash, diff against the committed table,
+// patch layout + metadata, gather of the dirty chunks.  With `from_shadow`
+// the kernels read the state from the shadow of an asynchronous checkpoint
+// and run on async_ctas(s) CTAs.
+int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t cap, bool from_shadow,
+                     GraphEntry **out)
+{
+    const AllocDesc *allocs = from_shadow ? s->d_allocs_shadow : s->d_allocs;
+    reset_call(s, dimg, cap);
+    TileShape shh = s->shape[SHAPE_HASH], shg = s->shape[SHAPE_GATHER];
+    if (from_shadow) shh.ctas = shg.ctas = async_ctas(s);
+    if (mode == SNAP_FULL) {
+        Job j = base_job(s, OP_GATHER);
+        j.allocs = allocs;
+        j.host = dimg;
+        j.hash_out = s->d_hash[cur];
+        s->h_cb->jobs[0] = j;
+        const CombineConsts cc = make_combine_consts(s->C, shg.piece);
+        return get_graph(s, from_shadow ? GK_ASYNC_FULL : GK_FULL, cur, [&](cudaStream_t q) {
+            cudaError_t e = enqueue_prologue(s, q);
+            if (e == cudaSuccess) e = launch_full_meta(allocs, s->desc.size(), s->C, &s->d_cb->cp, q);
+            if (e == cudaSuccess && s->n_chunks)
+                e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, shg, &s->d_cb->res, q);
+            if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+            return e;
+        }, out);
+    }
+    Job jh = base_job(s, OP_HASH);
+    jh.allocs = allocs;
+    jh.hash_out = s->d_hash[cur];
+    Job jg = base_job(s, OP_GATHER_DIRTY);
+    jg.allocs = allocs;
+    jg.host = dimg;
+    jg.tile_list = s->d_dlist;
+    jg.n_tiles_dev = &s->d_cb->res.n_dirty;
+    jg.patch_data = s->d_patch_data;
+    jg.dstart = s->d_dstart;
+    jg.cap_exceeded = &s->d_cb->res.cap_exceeded;
+    s->h_cb->jobs[0] = jh;
+    s->h_cb->jobs[1] = jg;
+    const CombineConsts cch = make_combine_consts(s->C, shh.piece);
+    const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
+    const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
+    return get_graph(s, from_shadow ? GK_ASYNC_INCR : GK_INCR, cur, [&](cudaStream_t q) {
+        cudaError_t e = enqueue_prologue(s, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cch, shh, &s->d_cb->res, q);
+        if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_HASH_END, q);
+        if (e == cudaSuccess)
+            e = launch_diff(curp, prevp, s->n_chunks, s->d_blockcnt, s->d_blockoff, s->d_dlist, &s->d_cb->res, q);
+        if (e == cudaSuccess)
+            e = launch_patch_layout(allocs, s->desc.size(), s->C, s->d_dlist, s->d_patch_rec, s->d_patch_data,
+                                    s->d_dstart, &s->d_cb->cp, &s->d_cb->res, q);
+        if (e == cudaSuccess)
+            e = launch_patch_meta(allocs, s->desc.size(), s->C, curp, s->d_dlist, s->d_patch_rec, s->d_patch_data,
+                                  s->d_dstart, &s->d_cb->res, &s->d_cb->cp, q);
+        if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_DIFF_END, q);
+        if (e == cudaSuccess && s->n_chunks)
+            e = launch_tiles(s->d_cb->jobs + 1, 1, &s->d_cb->cursor[1], ccg, shg, &s->d_cb->res, q);
+        if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+        return e;
+    }, out);
+}
+
+// After the device finished a checkpoint graph: write the image header,
+// fill the stats and commit the new hash table as the base (Sec. 3.1: only
+// a completed checkpoint replaces the base).
+int complete_checkpoint(snap_set_s *s, int mode, int cur, uint8_t *host_image, uint64_t *used, snap_stats &st)
+{
+    const uint64_t gen = s->next_gen;
+    if (mode == SNAP_FULL) {
+        write_header(host_image, SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(), s->total_bytes, gen, 0);
+        st.image_bytes = s->full_bytes;
+        st.copy_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
+        st.dirty_chunks = s->n_chunks;
+    } else {
+        if (s->h_res->cap_exceeded) return SNAP_EINVAL;
+        write_header(host_image, SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C, s->desc.size(),
+                     s->total_bytes, gen, s->base_gen);
+        st.image_bytes = s->h_res->patch_bytes;
+        st.dirty_chunks = s->h_res->n_dirty;
+        st.hash_ms = ts_ms(s, TS_BEGIN, TS_HASH_END);
+        st.diff_ms = ts_ms(s, TS_HASH_END, TS_DIFF_END);
+        st.copy_ms = ts_ms(s, TS_DIFF_END, TS_COPY_END);
+    }
+    if (used) *used = st.image_bytes;
+    s->prev_idx = cur;
+    s->has_base = true;
+    s->base_gen = gen;
+    s->next_gen = gen + 1;
+    st.state_bytes = s->total_bytes;
+    st.total_chunks = s->n_chunks;
+    st.generation = gen;
     return SNAP_OK;
 }
 
@@ -477,6 +587,7 @@ int snap_set_destroy(snap_set s)
     if (s->st) cudaStreamSynchronize(s->st);
     free_device(s);
     ring_free(s);
+    async_free(s);
     cudaFree(s->d_cb);
     cudaFreeHost(s->h_cb);
     cudaFreeHost(s->h_res);
@@ -512,7 +623,7 @@ int snap_register(snap_set s, void *dptr, uint64_t bytes)
 
 int snap_set_prepare(snap_set s, int what)
 {
-    if (!s || (what & ~(SNAP_PREPARE_LAYOUT | SNAP_PREPARE_RING))) return SNAP_EINVAL;
+    if (!s || (what & ~(SNAP_PREPARE_LAYOUT | SNAP_PREPARE_RING | SNAP_PREPARE_SHADOW))) return SNAP_EINVAL;
     BusyGuard g(s);
     if (!g.ok) return SNAP_EBUSY;
     cudaSetDevice(s->device);
@@ -521,6 +632,7 @@ int snap_set_prepare(snap_set s, int what)
         Ring *r = nullptr;
         rc = ring_get(s, &r);
     }
+    if (rc == SNAP_OK && (what & SNAP_PREPARE_SHADOW)) rc = async_prepare(s);
     return rc;
 }
 
@@ -562,91 +674,20 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
     if (!dimg) return ring_checkpoint(s, static_cast<uint8_t *>(host_image), cap, mode, used, t0, tq, deadline);
 
     const int cur = 1 - s->prev_idx;
-    const uint64_t gen = s->has_base ? s->next_gen : s->next_gen;
-    reset_call(s, dimg, cap);
+    GraphEntry *ge = nullptr;
+    rc = checkpoint_graph(s, mode, cur, dimg, cap, false, &ge);
+    if (rc) return rc;
+    s->call_kernels = ge->kernels;
+    rc = cuda_status(cudaGraphLaunch(ge->exec, s->st));
+    if (rc == SNAP_OK) rc = finish(s, deadline);
+    if (rc) return rc;
     snap_stats st{};
-    if (mode == SNAP_FULL) {
-        Job j = base_job(s, OP_GATHER);
-        j.host = dimg;
-        j.hash_out = s->d_hash[cur];
-        s->h_cb->jobs[0] = j;
-        const TileShape sh = s->shape[SHAPE_GATHER];
-        const CombineConsts cc = make_combine_consts(s->C, sh.piece);
-        rc = run_graph(s, GK_FULL, cur, [&](cudaStream_t q) {
-            cudaError_t e = enqueue_prologue(s, q);
-            if (e == cudaSuccess) e = launch_full_meta(s->d_allocs, s->desc.size(), s->C, &s->d_cb->cp, q);
-            if (e == cudaSuccess && s->n_chunks)
-                e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cc, sh, &s->d_cb->res, q);
-            if (e == cudaSuccess) e = enqueue_epilogue(s, q);
-            return e;
-        });
-        if (rc == SNAP_OK) rc = finish(s, deadline);
-        if (rc) return rc;
-        write_header(static_cast<uint8_t *>(host_image), SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(),
-                     s->total_bytes, gen, 0);
-        *used = s->full_bytes;
-        st.image_bytes = s->full_bytes;
-        st.copy_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
-        st.dirty_chunks = s->n_chunks;
-    } else {
-        Job jh = base_job(s, OP_HASH);
-        jh.hash_out = s->d_hash[cur];
-        Job jg = base_job(s, OP_GATHER_DIRTY);
-        jg.host = dimg;
-        jg.tile_list = s->d_dlist;
-        jg.n_tiles_dev = &s->d_cb->res.n_dirty;
-        jg.patch_data = s->d_patch_data;
-        jg.dstart = s->d_dstart;
-        jg.cap_exceeded = &s->d_cb->res.cap_exceeded;
-        s->h_cb->jobs[0] = jh;
-        s->h_cb->jobs[1] = jg;
-        const TileShape shh = s->shape[SHAPE_HASH];
-        const TileShape shg = s->shape[SHAPE_GATHER];
-        const CombineConsts cch = make_combine_consts(s->C, shh.piece);
-        const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
-        const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
-        rc = run_graph(s, GK_INCR, cur, [&](cudaStream_t q) {
-            cudaError_t e = enqueue_prologue(s, q);
-            if (e == cudaSuccess && s->n_chunks)
-                e = launch_tiles(s->d_cb->jobs, 1, &s->d_cb->cursor[0], cch, shh, &s->d_cb->res, q);
-            if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_HASH_END, q);
-            if (e == cudaSuccess)
-                e = launch_diff(curp, prevp, s->n_chunks, s->d_blockcnt, s->d_blockoff, s->d_dlist, &s->d_cb->res, q);
-            if (e == cudaSuccess)
-                e = launch_patch_layout(s->d_allocs, s->desc.size(), s->C, s->d_dlist, s->d_patch_rec,
-                                        s->d_patch_data, s->d_dstart, &s->d_cb->cp, &s->d_cb->res, q);
-            if (e == cudaSuccess)
-                e = launch_patch_meta(s->d_allocs, s->desc.size(), s->C, curp, s->d_dlist, s->d_patch_rec,
-                                      s->d_patch_data, s->d_dstart, &s->d_cb->res, &s->d_cb->cp, q);
-            if (e == cudaSuccess) e = launch_stamp(&s->d_cb->res, TS_DIFF_END, q);
-            if (e == cudaSuccess && s->n_chunks)
-                e = launch_tiles(s->d_cb->jobs + 1, 1, &s->d_cb->cursor[1], ccg, shg, &s->d_cb->res, q);
-            if (e == cudaSuccess) e = enqueue_epilogue(s, q);
-            return e;
-        });
-        if (rc == SNAP_OK) rc = finish(s, deadline);
-        if (rc) return rc;
-        if (s->h_res->cap_exceeded) return SNAP_EINVAL;
-        write_header(static_cast<uint8_t *>(host_image), SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C,
-                     s->desc.size(), s->total_bytes, gen, s->base_gen);
-        *used = s->h_res->patch_bytes;
-        st.image_bytes = s->h_res->patch_bytes;
-        st.dirty_chunks = s->h_res->n_dirty;
-        st.hash_ms = ts_ms(s, TS_BEGIN, TS_HASH_END);
-        st.diff_ms = ts_ms(s, TS_HASH_END, TS_DIFF_END);
-        st.copy_ms = ts_ms(s, TS_DIFF_END, TS_COPY_END);
-    }
-    // commit (Sec. 3.1: only a completed checkpoint replaces the base)
-    s->prev_idx = cur;
-    s->has_base = true;
-    s->base_gen = gen;
-    s->next_gen = gen + 1;
-    st.state_bytes = s->total_bytes;
-    st.total_chunks = s->n_chunks;
-    st.generation = gen;
+    rc = complete_checkpoint(s, mode, cur, static_cast<uint8_t *>(host_image), used, st);
+    if (rc) return rc;
     st.quiesce_ms = tq - t0;
     st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }
@@ -709,6 +750,7 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
     st.copy_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
     st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }
@@ -761,6 +803,7 @@ int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_
     st.hash_ms = ts_ms(s, TS_BEGIN, TS_COPY_END);
     st.kernel_launches = s->call_kernels;
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }
@@ -827,6 +870,7 @@ int snap_plain_checkpoint(snap_set s, void *host_image, uint64_t cap)
     st.state_bytes = s->total_bytes;
     st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }
@@ -862,6 +906,7 @@ int snap_plain_restore(const void *host_image, uint64_t bytes, snap_set s)
     st.state_bytes = s->total_bytes;
     st.copy_ms = ev_ms(s, EV_BEGIN, EV_COPY_END);
     st.total_ms = now_ms() - t0;
+    st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
 }

@@ -29,7 +29,7 @@ struct CallBlock {
 };
 
 enum EventId { EV_BEGIN = 0, EV_HASH_END, EV_DIFF_END, EV_COPY_END, EV_END, EV_COUNT };
-enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY };
+enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY, GK_ASYNC_FULL, GK_ASYNC_INCR };
 enum ShapeKind { SHAPE_GATHER = 0, SHAPE_HASH, SHAPE_SCATTER, SHAPE_COUNT };
 
 struct GraphEntry {
@@ -89,6 +89,18 @@ struct snap_set_s {
     uint64_t call_kernels = 0;  // kernels launched by the current call
 
     snapk::Ring *ring = nullptr;
+
+    // asynchronous checkpoint (async.cu)
+    uint8_t *d_shadow = nullptr;                // packed copy of the state at the cut
+    snapk::AllocDesc *d_allocs_shadow = nullptr;  // the allocation table pointing into it
+    uint64_t shadow_bytes = 0;
+    cudaStream_t st_bg = nullptr;               // lowest-priority stream for the background part
+    cudaEvent_t ev_bg = nullptr;               // end of the background part
+    std::atomic<bool> async_pending{false};
+    std::atomic<bool> async_waiting{false};
+    int async_mode = 0, async_cur = 0;
+    uint8_t *async_image = nullptr;
+    double async_t0 = 0, async_tq = 0, async_tcut = 0;
 };
 
 namespace snapk {
@@ -126,5 +138,27 @@ uint64_t parts_for(uint64_t bytes, int threads);
 
 // (Re)build a set's device layout after registrations (runtime.cu).
 int build_layout(snap_set_s *s);
+
+// Holds a set's busy flag for the duration of a call.
+struct BusyGuard {
+    snap_set_s *s;
+    bool ok;
+    explicit BusyGuard(snap_set_s *s_) : s(s_) { ok = !s->busy.exchange(true); }
+    ~BusyGuard() { if (ok) s->busy.store(false); }
+};
+
+// call plumbing (runtime.cu)
+int settle(snap_set_s *s, double deadline);   // wait for a timed-out earlier call
+int quiesce(snap_set_s *s, double deadline);  // drain the caller's stream
+int async_ctas(const snap_set_s *s);
+int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t cap, bool from_shadow,
+                     GraphEntry **out);
+int complete_checkpoint(snap_set_s *s, int mode, int cur, uint8_t *host_image, uint64_t *used, snap_stats &st);
+
+// asynchronous checkpoint resources (async.cu): the shadow and its table
+// (freed with the layout), the background stream and event (freed with the set)
+int async_prepare(snap_set_s *s);
+void async_free_layout(snap_set_s *s);
+void async_free(snap_set_s *s);
 
 }  // namespace snapk

@@ -319,6 +319,7 @@ void finish(snap_server_s *sv, SReq *r)
     r->st.total_chunks = s->n_chunks;
     r->st.generation = r->kind == SNAP_REQ_RESTORE ? r->h.generation : r->gen;
     r->st.total_ms = r->t_done - r->t_arrive;
+    r->st.frozen_ms = r->st.total_ms;
     r->st.quiesce_ms = r->t_admit - r->t_arrive;  // time queued before admission
     s->busy.store(false);
     sv->pinned_used -= r->pinned_charge;

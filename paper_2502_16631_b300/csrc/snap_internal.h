@@ -129,6 +129,11 @@ cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64
                               const uint64_t *patch_data, const uint64_t *dstart,
                               const Result *res, const CallParams *cp, cudaStream_t st);
 
+// Device-to-device copy of every allocation into the packed shadow buffer
+// (the cut of an asynchronous checkpoint).
+cudaError_t launch_shadow_copy(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes, uint64_t n_chunks,
+                               uint8_t *shadow, int sms, cudaStream_t st);
+
 // One-thread kernel recording the device clock into res->ts[idx]; stream
 // order makes it a phase boundary inside a captured graph.
 cudaError_t launch_stamp(Result *res, int idx, cudaStream_t st);
