@@ -62,7 +62,7 @@ def parse():
                         "matmul load, against the synchronous call")
     p.add_argument("--load-gemms", type=int, default=0, help="async: matmuls per step (0: about 3x the "
                    "background part)")
-    p.add_argument("--async-ctas", default="0,8,16,74", help="async: background grids to measure (0: the "
+    p.add_argument("--async-ctas", default="0,4,37", help="async: background grids to measure (0: the "
                    "library default, which gives the reported value)")
     p.add_argument("--arrivals", type=int, default=1200, help="serving: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
@@ -1029,7 +1029,7 @@ def run_async(args, rank, world, local, pg):
                               "under %d bf16 8192^3 matmuls on the caller's stream" % n,
                   "step": "load alone; sync checkpoint + load; async checkpoint + load + wait",
                   "l2": "2.26 GB state, larger than L2"},
-                 {"async": {"default_ctas": max(1, torch.cuda.get_device_properties(0).multi_processor_count // 4),
+                 {"async": {"default_ctas": 8,
                             "by_ctas": {str(k): v for k, v in sweep.items()},
                             "sync_checkpoint_ms": med(sync_ms), "load_ms": med(L), "sync_step_ms": med(S),
                             "caller_cost_sync_ms": over_sync, "sync_equivalent_gbs": B / (over_sync * 1e-3) / 1e9,

@@ -81,7 +81,7 @@ typedef struct {
     uint32_t stages;       /* staging buffers per warp; 0 = tuned default */
     uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB */
     uint32_t async_ctas;   /* CTAs of the background part of snap_checkpoint_async;
-                              default a quarter of the SMs */
+                              default 8 (enough to saturate the host link) */
 } snap_opts;
 
 /* Per-call statistics (times in milliseconds; quiesce_ms and total_ms are
@@ -165,8 +165,10 @@ SNAP_API int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mod
  * registered allocation device to device into a library-owned shadow
  * buffer (the cut), and return; the caller may then modify its allocations
  * freely.  Hashing, diffing and the transfer into host_image (pinned and
- * mapped: snap_host_alloc memory) run from the shadow on a lowest-priority
+ * mapped: snap_host_alloc memory) run from the shadow on a least-priority
  * stream with opts.async_ctas CTAs, leaving the other SMs to the caller.
+ * snap_last_stats after the wait: frozen_ms = entry to return of this call,
+ * total_ms = entry to the commit in snap_checkpoint_wait.
  * The result is exactly what snap_checkpoint would have produced at the
  * cut.  The set stays busy (EBUSY for other calls) until
  * snap_checkpoint_wait.  The shadow (the packed size of the state) is

@@ -392,7 +392,10 @@ static int finish(snap_set_s *s, double deadline)
 
 int async_ctas(const snap_set_s *s)
 {
-    const int c = s->opts.async_ctas ? (int)s->opts.async_ctas : s->sms / 4;
+    // the background gather is bound by the host link, which 8 CTAs
+    // saturate on B300 (about 7 GB/s each); more would only take SMs from
+    // the caller
+    const int c = s->opts.async_ctas ? (int)s->opts.async_ctas : 8;
     return std::max(1, std::min(c, s->sms));
 }
 
