@@ -188,6 +188,37 @@ SNAP_API int snap_checkpoint_wait(snap_set s, uint32_t timeout_ms, uint64_t *use
  * base.  Errors: EINVAL, EFORMAT, EMISMATCH, ETIMEDOUT, EBUSY, ECUDA. */
 SNAP_API int snap_restore(const void *host_image, uint64_t bytes, snap_set s);
 
+/* Prioritised restore (the on-demand restore Sec. 7 cites from Yang et al.:
+ * what the application needs first is restored first).  Validates the image
+ * as snap_restore does, quiesces the caller's stream and queues the scatter
+ * in priority order: the n_first allocations listed in `first` (indices as
+ * snap_register returned them, no repeats; may be empty) form wave 0, the
+ * other allocations follow in index order in waves of doubling size (the
+ * first at least 64 MiB; at most SNAP_RESTORE_MAX_WAVES waves).  Returns
+ * once the waves are queued.  snap_restore_ready makes a stream wait for one
+ * allocation; snap_restore_wait finishes the restore.  Until then the set
+ * answers SNAP_EBUSY to other calls, and the image (pinned and mapped:
+ * snap_host_alloc memory) must stay untouched.  Errors as snap_restore, plus
+ * EINVAL for a pageable image or a bad `first` list. */
+#define SNAP_RESTORE_MAX_WAVES 16u
+SNAP_API int snap_restore_async(const void *host_image, uint64_t bytes, snap_set s, const uint32_t *first,
+                                uint32_t n_first);
+
+/* Make `stream` (a cudaStream_t; NULL: the set's stream) wait, without
+ * blocking the host, until allocation `index` of the pending prioritised
+ * restore is in place.  With no restore pending the allocation is already
+ * in place and it returns SNAP_OK.  EINVAL for an index out of range.  Not
+ * to be called concurrently with snap_restore_wait on the same set. */
+SNAP_API int snap_restore_ready(snap_set s, uint32_t index, void *stream);
+
+/* Wait up to timeout_ms for the pending prioritised restore; on completion
+ * adopt the image's hashes and generation as the committed base (as
+ * snap_restore does) and return its status.  ETIMEDOUT leaves it pending;
+ * EINVAL if none is pending.  snap_last_stats afterwards: frozen_ms = call
+ * entry until wave 0 was in place, total_ms = call entry until the commit,
+ * copy_ms = device time of all waves. */
+SNAP_API int snap_restore_wait(snap_set s, uint32_t timeout_ms);
+
 /* Re-hash the device state and compare every chunk with the hashes stored in
  * host_image (a full image or a patch).  *n_mismatch = number of differing
  * chunks.  Sec. 6 (a restore must reproduce the snapshotted state). */

@@ -33,7 +33,7 @@ REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 EXPORTS = (
     "snap_set_create", "snap_set_destroy", "snap_set_prepare", "snap_register", "snap_image_bytes",
     "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_checkpoint_async", "snap_checkpoint_wait",
-    "snap_restore", "snap_verify",
+    "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
     "snap_autotune",
@@ -98,6 +98,9 @@ def _lib():
             "snap_checkpoint_async": [vp, vp, u64, i32],
             "snap_checkpoint_wait": [vp, u32, P(u64)],
             "snap_restore": [vp, u64, vp],
+            "snap_restore_async": [vp, u64, vp, vp, u32],
+            "snap_restore_ready": [vp, u32, vp],
+            "snap_restore_wait": [vp, u32],
             "snap_verify": [vp, u64, vp, P(u64)],
             "snap_apply_patch": [vp, u64, vp, u64],
             "snap_committed_hashes": [vp, vp, u64, P(u64)],
@@ -257,6 +260,27 @@ class Set:
 
     def restore(self, image, nbytes: int | None = None) -> None:
         _check(self.restore_status(image, nbytes), "snap_restore")
+
+    def restore_async(self, image, first=(), nbytes: int | None = None) -> None:
+        """Start a prioritised restore: the allocations in `first` come back
+        first, the rest follow in waves."""
+        _check(self.restore_async_status(image, first, nbytes), "snap_restore_async")
+
+    def restore_async_status(self, image, first=(), nbytes: int | None = None) -> int:
+        arr = (ctypes.c_uint32 * max(1, len(first)))(*first)
+        return _lib().snap_restore_async(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+                                         ctypes.cast(arr, ctypes.c_void_p), len(first))
+
+    def restore_ready(self, index: int, stream=None) -> None:
+        """Make `stream` (torch stream or handle; None: the set's) wait for
+        allocation `index` of the pending prioritised restore."""
+        _check(_lib().snap_restore_ready(self.h, index, _stream_handle(stream)), "snap_restore_ready")
+
+    def restore_wait(self, timeout_ms: int = 60000) -> None:
+        _check(self.restore_wait_status(timeout_ms), "snap_restore_wait")
+
+    def restore_wait_status(self, timeout_ms: int = 60000) -> int:
+        return _lib().snap_restore_wait(self.h, timeout_ms)
 
     def restore_status(self, image, nbytes: int | None = None) -> int:
         return _lib().snap_restore(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h)

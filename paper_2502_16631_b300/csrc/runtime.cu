@@ -182,6 +182,7 @@ static void free_device(snap_set_s *s)
     s->d_patch_rec = s->d_patch_data = s->d_dstart = nullptr;
     s->h_hash_stage = nullptr;
     async_free_layout(s);
+    lazy_free_layout(s);
 }
 
 int build_layout(snap_set_s *s)
@@ -591,6 +592,7 @@ int snap_set_destroy(snap_set s)
     free_device(s);
     ring_free(s);
     async_free(s);
+    lazy_free(s);
     cudaFree(s->d_cb);
     cudaFreeHost(s->h_cb);
     cudaFreeHost(s->h_res);

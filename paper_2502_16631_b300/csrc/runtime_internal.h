@@ -101,6 +101,19 @@ struct snap_set_s {
     int async_mode = 0, async_cur = 0;
     uint8_t *async_image = nullptr;
     double async_t0 = 0, async_tq = 0, async_tcut = 0;
+
+    // prioritised restore (lazy.cu)
+    uint32_t *h_order = nullptr;                  // pinned: chunk indices in restore order
+    unsigned long long *d_wave_cursor = nullptr;  // one tile cursor per wave
+    cudaEvent_t ev_wave[SNAP_RESTORE_MAX_WAVES] = {};
+    cudaEvent_t ev_rstart = nullptr;
+    std::vector<int> wave_of;                     // wave of each allocation
+    int n_waves = 0;
+    std::atomic<bool> restore_pending{false};
+    std::atomic<bool> restore_waiting{false};
+    int restore_cur = 0;
+    uint64_t restore_gen = 0;
+    double restore_t0 = 0, restore_tq = 0, restore_tlaunch = 0;
 };
 
 namespace snapk {
@@ -160,5 +173,10 @@ int complete_checkpoint(snap_set_s *s, int mode, int cur, uint8_t *host_image, u
 int async_prepare(snap_set_s *s);
 void async_free_layout(snap_set_s *s);
 void async_free(snap_set_s *s);
+
+// prioritised restore resources (lazy.cu): the pinned order list (freed with
+// the layout), the wave cursors and events (freed with the set)
+void lazy_free_layout(snap_set_s *s);
+void lazy_free(snap_set_s *s);
 
 }  // namespace snapk
