@@ -54,13 +54,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-bytes", type=int, default=512 * MiB)
     p.add_argument("--workload", default="gpt2",
-                   choices=["gpt2", "random64m", "incr20g", "llama7b", "serving", "async", "lazy"],
+                   choices=["gpt2", "random64m", "incr20g", "llama7b", "serving", "async", "lazy", "file"],
                    help="gpt2: GPT-2-small training state (default); random64m: 16 random allocations, "
                         "64 MiB; incr20g: 20 GiB incremental at 1/10/50%% dirty with the chunk-size sweep; "
                         "llama7b: 115.8 GB Llama-7B state through the pinned ring; serving: 32 tenants, "
                         "Poisson arrivals; async: GPT-2 state checkpointed asynchronously under a bf16 "
                         "matmul load, against the synchronous call; lazy: GPT-2 state restored weights "
-                        "first, time until the weights are usable")
+                        "first, time until the weights are usable; file: GPT-2 state checkpointed to and "
+                        "restored from an image file")
+    p.add_argument("--file-dir", default=None, help="file: directory for the image files (default: the "
+                   "system temporary directory)")
     p.add_argument("--load-gemms", type=int, default=0, help="async: matmuls per step (0: about 3x the "
                    "background part)")
     p.add_argument("--async-ctas", default="0,4,37", help="async: background grids to measure (0: the "
@@ -1160,6 +1163,163 @@ def run_lazy(args, rank, world, local, pg):
     print(json.dumps(line))
 
 
+def run_file(args, rank, world, local, pg):
+    """GPT-2-small training state (593 allocations, 2,259,472,384 B) persisted
+    to an image file.  Per step:
+      overlapped   snap_checkpoint_file: windows written while the GPU
+                   gathers the next ones (page cache; and with fsync);
+      sequential   snap_checkpoint into pinned memory, then one write of the
+                   image to a file (the paper's order: device copy, then the
+                   memory write), same fsync rule;
+      restore      snap_restore_file (file in the page cache).
+      incremental  snap_checkpoint_file(INCREMENTAL) after a 10 % clustered
+                   mutation (the patch alone is written), with fsync.
+    `value` = state bytes / overlapped checkpoint time (with fsync); the
+    roofline peak is the storage itself: 2 GiB written by 8 threads with
+    pwrite, then fsync, measured in the same run."""
+    import shutil
+    import threading
+    import torch
+    import oracle
+    import paper_2502_16631_b300 as snap
+    spec = workloads.gpt2_state_spec()
+    sizes = workloads.spec_bytes(spec)
+    B = sum(sizes)
+    d = args.file_dir or tempfile.gettempdir()
+    free = shutil.disk_usage(d).free
+    if free < 3 * B:
+        print(json.dumps({"metric": "checkpoint to file GB/s", "unavailable":
+                          "%s has %d free bytes, needs %d" % (d, free, 3 * B)}))
+        return
+    ts = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+    workloads.torch_fill_spec(ts, spec, seed=args.seed)
+    s = snap.Set(chunk_bytes=UNIT)
+    for t in ts:
+        s.register(t)
+    s.prepare(layout=True, ring=True)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    path = os.path.join(d, "snap_bench_%d.img" % os.getpid())
+    seq_path = path + ".seq"
+    # parity at full size: the file equals the in-memory image; sampled
+    # chunks equal the device bytes; restore from the file verifies clean
+    used = s.checkpoint_file(path, snap.FULL)
+    s.checkpoint(img, snap.FULL)
+    fimg = np.fromfile(path, dtype=np.uint8)
+    same_header_free = bool(np.array_equal(fimg[64:], img.view(used)[64:]))
+    del fimg
+    rng = np.random.default_rng(args.seed)
+    samples = []
+    for k in sorted(set(rng.integers(0, len(sizes), 32).tolist())):
+        lo = int(rng.integers(0, max(1, sizes[k] // UNIT))) * UNIT
+        samples.append((k, lo, min(lo + UNIT, sizes[k])))
+
+    def seq(sync):
+        s.checkpoint(img, snap.FULL)
+        with open(seq_path, "wb") as f:
+            f.write(memoryview(img.array))
+            if sync:
+                f.flush()
+                os.fsync(f.fileno())
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    def storage_peak(nbytes=2 * GiB, threads=8):
+        buf = np.frombuffer(np.random.default_rng(0).bytes(64 * MiB), dtype=np.uint8)
+        fd = os.open(seq_path, os.O_CREAT | os.O_TRUNC | os.O_WRONLY, 0o644)
+        per = nbytes // threads
+
+        def worker(i):
+            off = i * per
+            while off < (i + 1) * per:
+                off += os.pwrite(fd, buf, off)
+
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=worker, args=(i,)) for i in range(threads)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        os.fsync(fd)
+        dt = time.perf_counter() - t0
+        os.close(fd)
+        return nbytes / dt / 1e9
+
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    units = workloads.mutation_units(int(starts[-1] // UNIT), args.dirty, args.seed)
+
+    def mutate():
+        flat = [(int(np.searchsorted(starts, u * UNIT, side="right") - 1), u) for u in units]
+        for k, u in flat:
+            lo = u * UNIT - int(starts[k])
+            if 0 <= lo < sizes[k]:
+                ts[k][lo: min(lo + UNIT, sizes[k])].bitwise_not_()
+
+    def incr():
+        mutate()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u = s.checkpoint_file(path + ".patch", snap.INCREMENTAL, sync=True)
+        return time.perf_counter() - t0, u
+
+    for _ in range(max(3, args.warmup)):
+        s.checkpoint_file(path, snap.FULL)
+        seq(False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    O, OS, Q, QS, R, kern = [], [], [], [], [], 0
+    for _ in range(args.steps):
+        O.append(timed(lambda: s.checkpoint_file(path, snap.FULL)))
+        kern += s.stats()["kernel_launches"]
+        OS.append(timed(lambda: s.checkpoint_file(path, snap.FULL, sync=True)))
+        kern += s.stats()["kernel_launches"]
+        Q.append(timed(lambda: seq(False)))
+        QS.append(timed(lambda: seq(True)))
+        R.append(timed(lambda: s.restore_file(path)))
+        kern += s.stats()["kernel_launches"]
+    I = [incr() for _ in range(args.steps)]
+    clk = clocks.stop()
+    speak = storage_peak()
+    host = {k: ts[k][lo:hi].cpu().numpy() for k, lo, hi in samples}
+    for t in ts:
+        t.zero_()
+    s.restore_file(path)
+    ok = same_header_free and all(np.array_equal(ts[k][lo:hi].cpu().numpy(), host[k]) for k, lo, hi in samples)
+    mism = s.verify(img, used)
+    med = statistics.median
+    g = lambda x: B / med(x) / 1e9  # noqa: E731
+    peaks = link_peak(torch)
+    line = _line(args, world, g(OS), med(OS) * 1e3,
+                 {"workload": "GPT-2-small training state, 593 allocations, 2,259,472,384 B, 64 KiB chunks, "
+                              "image file on %s" % d,
+                  "step": "overlapped checkpoint to file (with and without fsync), sequential checkpoint then "
+                          "write, restore from file",
+                  "l2": "2.26 GB state, larger than L2"},
+                 {"file": {"overlapped_gbs": g(O), "overlapped_fsync_gbs": g(OS), "sequential_gbs": g(Q),
+                           "sequential_fsync_gbs": g(QS), "restore_gbs": g(R),
+                           "overlap_speedup": med(Q) / med(O), "overlap_speedup_fsync": med(QS) / med(OS),
+                           "incremental_10pct_fsync_gbs": B / med([x[0] for x in I]) / 1e9,
+                           "incremental_patch_bytes": med([x[1] for x in I]),
+                           "storage_write_peak_gbs": speak, "d2h_link_gbs": peaks["d2h"]},
+                  "roofline": {"bound": "storage", "kernel": "ring checkpoint to file (gather + pwrite + fsync)",
+                               "achieved": g(OS), "peak": speak, "unit": "GB/s", "frac": g(OS) / speak,
+                               "note": "peak = 8-thread pwrite + fsync of 2 GiB to the same directory, this run"},
+                  "parity": {"file_equals_memory_image": same_header_free, "sampled_chunks": len(samples),
+                             "restore_bytes_equal": bool(ok), "verify_mismatches": mism},
+                  "clocks": clk, "gpu_launches": kern,
+                  "e2e": {"value": g(OS), "unit": "GB/s", "h2d_bytes_per_step": B, "d2h_bytes_per_step": 2 * used}})
+    line["metric"] = "checkpoint to an image file (fsync), GB/s of state"
+    for p in (path, seq_path, path + ".patch"):
+        try:
+            os.unlink(p)
+        except OSError:
+            pass
+    print(json.dumps(line))
+
+
 def _first_n(sizes, cap):
     tot, n = 0, 0
     for x in sizes:
@@ -1179,7 +1339,8 @@ def main():
         run_snap(args, rank, world, local, pg)
     else:
         {"random64m": run_random64m, "incr20g": run_incr20g, "llama7b": run_llama7b,
-         "serving": run_serving, "async": run_async, "lazy": run_lazy}[args.workload](args, rank, world, local, pg)
+         "serving": run_serving, "async": run_async, "lazy": run_lazy,
+         "file": run_file}[args.workload](args, rank, world, local, pg)
     if pg is not None:
         pg.destroy_process_group()
 

@@ -17,8 +17,9 @@
  *    memory; the library owns what it allocates (hash tables, descriptors,
  *    graphs, the pinned ring) and frees it in the matching destroy call.
  *  - Calls are synchronous: when a call returns SNAP_OK the image (checkpoint)
- *    or the device buffers (restore) are complete.  The serving API is the
- *    asynchronous form.
+ *    or the device buffers (restore) are complete.  The exceptions are
+ *    snap_checkpoint_async and snap_restore_async, completed by their _wait
+ *    calls (the set stays busy in between), and the serving API.
  *  - One call at a time per set: a call that finds another in progress on the
  *    same set returns SNAP_EBUSY.  Different sets may be used concurrently.
  *  - Failure atomicity (the plugin exit callback rolls back on error,
@@ -58,7 +59,9 @@ typedef enum {
                              sizes differ, or patch/base generations differ
                              (restore needs a compatible target, Sec. 4.4)  */
     SNAP_EBUSY = -8,      /* another call is in progress on this set        */
-    SNAP_EBUDGET = -9     /* request can never fit the server's budgets     */
+    SNAP_EBUDGET = -9,    /* request can never fit the server's budgets     */
+    SNAP_EIO = -10        /* opening, reading, writing or renaming an image
+                             file failed                                    */
 } snap_status;
 
 typedef enum { SNAP_FULL = 0, SNAP_INCREMENTAL = 1 } snap_mode;
@@ -187,6 +190,27 @@ SNAP_API int snap_checkpoint_wait(snap_set s, uint32_t timeout_ms, uint64_t *use
  * be merged with snap_apply_patch).  The image's hashes become the committed
  * base.  Errors: EINVAL, EFORMAT, EMISMATCH, ETIMEDOUT, EBUSY, ECUDA. */
 SNAP_API int snap_restore(const void *host_image, uint64_t bytes, snap_set s);
+
+/* Persist a checkpoint straight to storage (the "memory write" stage of the
+ * paper's checkpoint, Table 2), overlapped with the gather: windows of the
+ * state stream through the set's pinned ring and host workers write each
+ * window to the file as soon as the GPU has filled it, so the device-to-host
+ * link and the storage work at the same time.  The image (full or patch,
+ * byte-identical to what snap_checkpoint writes into memory) goes to
+ * "<path>.tmp", which is renamed to `path` only after the whole image is
+ * written (and, with SNAP_FILE_SYNC, flushed to the device with fsync), so
+ * `path` never holds a partial image; on any failure the temporary file is
+ * removed and nothing is committed.  *used = image bytes.  The completion
+ * deadline is timeout_ms plus the image size at 64 MB/s.  Errors as
+ * snap_checkpoint, plus EIO. */
+#define SNAP_FILE_SYNC 1
+SNAP_API int snap_checkpoint_file(snap_set s, const char *path, int mode, int flags, uint64_t *used);
+
+/* Restore a full image file written by snap_checkpoint_file (or any full
+ * image saved to a file), overlapping the reads with the scatter through the
+ * pinned ring.  The header and every record are read and validated before
+ * any device byte changes.  Errors as snap_restore, plus EIO. */
+SNAP_API int snap_restore_file(const char *path, snap_set s);
 
 /* Prioritised restore (the on-demand restore Sec. 7 cites from Yang et al.:
  * what the application needs first is restored first).  Validates the image

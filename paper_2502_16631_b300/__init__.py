@@ -24,8 +24,9 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsnap.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGET = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGET, EIO = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
+FILE_SYNC = 1
 FULL, INCREMENTAL = 0, 1
 REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 
@@ -33,7 +34,7 @@ REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 EXPORTS = (
     "snap_set_create", "snap_set_destroy", "snap_set_prepare", "snap_register", "snap_image_bytes",
     "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_checkpoint_async", "snap_checkpoint_wait",
-    "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
+    "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
     "snap_autotune",
@@ -98,6 +99,8 @@ def _lib():
             "snap_checkpoint_async": [vp, vp, u64, i32],
             "snap_checkpoint_wait": [vp, u32, P(u64)],
             "snap_restore": [vp, u64, vp],
+            "snap_checkpoint_file": [vp, ctypes.c_char_p, i32, i32, P(u64)],
+            "snap_restore_file": [ctypes.c_char_p, vp],
             "snap_restore_async": [vp, u64, vp, vp, u32],
             "snap_restore_ready": [vp, u32, vp],
             "snap_restore_wait": [vp, u32],
@@ -260,6 +263,24 @@ class Set:
 
     def restore(self, image, nbytes: int | None = None) -> None:
         _check(self.restore_status(image, nbytes), "snap_restore")
+
+    def checkpoint_file(self, path: str, mode: int = FULL, sync: bool = False) -> int:
+        """Checkpoint straight into a file (written as <path>.tmp, renamed when complete)."""
+        rc, used = self.checkpoint_file_status(path, mode, sync)
+        _check(rc, "snap_checkpoint_file")
+        return used
+
+    def checkpoint_file_status(self, path: str, mode: int = FULL, sync: bool = False):
+        used = ctypes.c_uint64()
+        rc = _lib().snap_checkpoint_file(self.h, os.fsencode(path), mode, FILE_SYNC if sync else 0,
+                                         ctypes.byref(used))
+        return rc, used.value
+
+    def restore_file(self, path: str) -> None:
+        _check(self.restore_file_status(path), "snap_restore_file")
+
+    def restore_file_status(self, path: str) -> int:
+        return _lib().snap_restore_file(os.fsencode(path), self.h)
 
     def restore_async(self, image, first=(), nbytes: int | None = None) -> None:
         """Start a prioritised restore: the allocations in `first` come back

@@ -174,6 +174,34 @@ void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8
     }
 }
 
+// copy_window_part for an ImageIO end (memory or file); false after an I/O error.
+static bool copy_window_io(const snap_set_s *s, const Window &w, uint8_t *slot, ImageIO &io, uint64_t p0, uint64_t p1,
+                           bool to_image)
+{
+    if (io.mem) {
+        copy_window_part(s, w, slot, io.mem, p0, p1, to_image);
+        return true;
+    }
+    const uint64_t lo = w.b0 + p0, hi = w.b0 + p1;
+    size_t k = 0;
+    {
+        size_t a = 0, b = s->desc.size();
+        while (b - a > 1) {
+            const size_t m = (a + b) / 2;
+            if (s->desc[m].state_off <= lo) a = m; else b = m;
+        }
+        k = a;
+    }
+    for (; k < s->desc.size() && s->desc[k].state_off < hi; ++k) {
+        const AllocDesc &a = s->desc[k];
+        const uint64_t x0 = std::max(lo, a.state_off), x1 = std::min(hi, a.state_off + a.bytes);
+        if (x1 <= x0) continue;
+        if (to_image) io.put(a.data_off + (x0 - a.state_off), slot + (x0 - w.b0), x1 - x0);
+        else io.get(a.data_off + (x0 - a.state_off), slot + (x0 - w.b0), x1 - x0);
+    }
+    return io.err.load() == 0;
+}
+
 static Job window_job(const snap_set_s *s, Ring *r, int slot, uint32_t op, const Window &w, uint32_t *hash_out)
 {
     Job j{};
@@ -226,7 +254,7 @@ static void drain(Progress &pg)
 }
 
 // --------------------------------------------------------------- checkpoint
-static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, double deadline, int cur, snap_stats &st)
+static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double deadline, int cur, snap_stats &st)
 {
     if (cap < s->full_bytes) return SNAP_EINVAL;
     const std::vector<Window> win = make_windows(s, r->slot_bytes);
@@ -265,8 +293,8 @@ static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, doubl
                     const int q = wait_event(r->ev[slot], deadline);  // ETIMEDOUT or ECUDA
                     if (q) pg.err = q;
                 }
-                if (!pg.err)
-                    copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, image, p0, p1, true);
+                if (!pg.err && !copy_window_io(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, io, p0, p1, true))
+                    pg.err = SNAP_EIO;
                 pg.done(w);
             });
         }
@@ -291,11 +319,12 @@ static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, doubl
         const AllocDesc &a = s->desc[k];
         const uint64_t nk = (a.bytes + s->C - 1) / s->C;
         const uint64_t rec[4] = {a.bytes, nk, a.data_off, 0};
-        std::memcpy(image + a.rec_off, rec, 32);
-        std::memcpy(image + a.rec_off + 32, s->h_hash_stage + a.chunk0, 4 * nk);
-        std::memset(image + a.rec_off + 32 + 4 * nk, 0, a.data_off - (a.rec_off + 32 + 4 * nk));
-        std::memset(image + a.data_off + a.bytes, 0, upg(a.data_off + a.bytes) - (a.data_off + a.bytes));
+        io.put(a.rec_off, rec, 32);
+        io.put(a.rec_off + 32, s->h_hash_stage + a.chunk0, 4 * nk);
+        io.zero(a.rec_off + 32 + 4 * nk, a.data_off - (a.rec_off + 32 + 4 * nk));
+        io.zero(a.data_off + a.bytes, upg(a.data_off + a.bytes) - (a.data_off + a.bytes));
     }
+    if (io.err) return io.err;
     st.image_bytes = s->full_bytes;
     st.dirty_chunks = s->n_chunks;
     st.kernel_launches = W;
@@ -305,7 +334,7 @@ static int ring_full(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, doubl
 // Incremental into a pageable patch: device hash + diff + layout as in the
 // direct path, metadata written by the host from the copied-back tables, and
 // the dirty chunks streamed through the ring one C-byte slot each.
-static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap, double deadline, int cur,
+static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double deadline, int cur,
                             uint64_t *used, snap_stats &st)
 {
     std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
@@ -350,24 +379,23 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
     if (e == cudaSuccess && s->n_chunks)
         e = cudaMemcpy(s->h_hash_stage, curp, s->n_chunks * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
-    // metadata
+    // metadata: record, all hashes, dirty count and index list per allocation
+    std::vector<uint32_t> meta;
     for (size_t k = 0; k < na; ++k) {
         const AllocDesc &a = s->desc[k];
         const uint64_t nk = (a.bytes + s->C - 1) / s->C;
         const uint64_t ndk = dst[k + 1] - dst[k];
         const uint64_t rec[4] = {a.bytes, nk, pdat[k], 0};
-        uint8_t *p = image + prec[k];
-        std::memcpy(p, rec, 32);
-        std::memcpy(p + 32, s->h_hash_stage + a.chunk0, 4 * nk);
-        const uint32_t n32 = (uint32_t)ndk;
-        std::memcpy(p + 32 + 4 * nk, &n32, 4);
-        for (uint64_t j = 0; j < ndk; ++j) {
-            const uint32_t idx = dl[dst[k] + j] - (uint32_t)a.chunk0;
-            std::memcpy(p + 36 + 4 * nk + 4 * j, &idx, 4);
-        }
+        meta.resize(8 + nk + 1 + ndk);
+        std::memcpy(meta.data(), rec, 32);
+        std::memcpy(meta.data() + 8, s->h_hash_stage + a.chunk0, 4 * nk);
+        meta[8 + nk] = (uint32_t)ndk;
+        for (uint64_t j = 0; j < ndk; ++j) meta[9 + nk + j] = dl[dst[k] + j] - (uint32_t)a.chunk0;
+        io.put(prec[k], meta.data(), 4 * meta.size());
         const uint64_t z = prec[k] + 36 + 4 * nk + 4 * ndk;
-        std::memset(image + z, 0, pdat[k] - z);
+        io.zero(z, pdat[k] - z);
     }
+    if (io.err) return io.err;
     // dirty data: windows of whole C-byte slots over the dirty ranks
     const uint64_t per = r->slot_bytes / s->C;
     const size_t W = (size_t)((nd + per - 1) / per);
@@ -421,8 +449,9 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
                     const AllocDesc &a = s->desc[k];
                     const uint64_t i = c - a.chunk0;
                     const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
-                    stream_copy(image + pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
+                    io.put(pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
                 }
+                if (io.err) pg.err = SNAP_EIO;
             }
             pg.done(w);
         });
@@ -445,7 +474,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, uint8_t *image, uint64_t cap
     return SNAP_OK;
 }
 
-int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
+int ring_checkpoint(snap_set_s *s, ImageIO &io, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
                     double deadline)
 {
     Ring *r = nullptr;
@@ -454,17 +483,20 @@ int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint6
     const int cur = 1 - s->prev_idx;
     const uint64_t gen = s->next_gen;
     snap_stats st{};
+    uint8_t hdr[SNAP_IMG_HEADER_BYTES];
     if (mode == SNAP_FULL) {
-        rc = ring_full(s, r, image, cap, deadline, cur, st);
+        rc = ring_full(s, r, io, cap, deadline, cur, st);
         if (rc) return rc;
-        write_header(image, SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(), s->total_bytes, gen, 0);
+        write_header(hdr, SNAP_IMG_FLAG_DEVICE_STATE, s->C, s->desc.size(), s->total_bytes, gen, 0);
         *used = s->full_bytes;
     } else {
-        rc = ring_incremental(s, r, image, cap, deadline, cur, used, st);
+        rc = ring_incremental(s, r, io, cap, deadline, cur, used, st);
         if (rc) return rc;
-        write_header(image, SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C, s->desc.size(),
+        write_header(hdr, SNAP_IMG_FLAG_DEVICE_STATE | SNAP_IMG_FLAG_INCREMENTAL, s->C, s->desc.size(),
                      s->total_bytes, gen, s->base_gen);
     }
+    io.put(0, hdr, sizeof hdr);
+    if (io.err) return io.err;
     s->prev_idx = cur;
     s->has_base = true;
     s->base_gen = gen;
@@ -480,10 +512,8 @@ int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint6
 }
 
 // ------------------------------------------------------------------ restore
-int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const ImageHeader &h, double t0, double tq,
-                 double deadline)
+int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, double tq, double deadline)
 {
-    (void)bytes;
     Ring *r = nullptr;
     int rc = ring_get(s, &r);
     if (rc) return rc;
@@ -501,7 +531,6 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
     const TileShape sh = s->shape[SHAPE_SCATTER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
     const double tc0 = now_ms();
-    uint8_t *img = const_cast<uint8_t *>(image);  // read only: copies run image -> slot
 
     // queue the fill of window w: it waits for the kernel of window w - slots
     auto queue_fill = [&](size_t w) {
@@ -524,8 +553,8 @@ int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const Imag
                         if (q) pg.err = q;
                     }
                 }
-                if (!pg.err)
-                    copy_window_part(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, img, p0, p1, false);
+                if (!pg.err && !copy_window_io(s, win[w], r->host + (uint64_t)slot * r->slot_bytes, io, p0, p1, false))
+                    pg.err = SNAP_EIO;
                 pg.done(w);
             });
         }

@@ -114,7 +114,7 @@ int parse_header(const uint8_t *img, uint64_t len, ImageHeader *h)
 // Walk an image's records (full or patch) against the set's allocations,
 // collecting every chunk hash into `hashes` (global chunk order).  For a full
 // image also checks that every data offset is where the layout puts it.
-int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes)
+int walk_records_io(const snap_set_s *s, const ImageReader &rd, uint64_t len, const ImageHeader &h, uint32_t *hashes)
 {
     if (h.chunk_bytes != s->C) return SNAP_EMISMATCH;
     if (h.n_allocs != s->allocs.size()) return SNAP_EMISMATCH;
@@ -125,12 +125,12 @@ int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const Im
         const AllocDesc &a = s->desc[k];
         if (off + 32 > len) return SNAP_EFORMAT;
         uint64_t rec[4];
-        std::memcpy(rec, img + off, 32);
+        if (!rd(off, rec, 32)) return SNAP_EIO;
         if (rec[0] != a.bytes) return SNAP_EMISMATCH;
         const uint64_t nk = (a.bytes + s->C - 1) / s->C;
         if (rec[1] != nk || rec[3] != 0) return SNAP_EFORMAT;
         if (nk > (len - off - 32) / 4) return SNAP_EFORMAT;
-        if (hashes) std::memcpy(hashes + a.chunk0, img + off + 32, 4 * nk);
+        if (hashes && nk && !rd(off + 32, hashes + a.chunk0, 4 * nk)) return SNAP_EIO;
         if (!patch) {
             if (rec[2] != a.data_off || off != a.rec_off) return SNAP_EFORMAT;
             if (a.data_off > len || a.bytes > len - a.data_off) return SNAP_EFORMAT;
@@ -138,14 +138,14 @@ int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const Im
         } else {
             if (off + 36 + 4 * nk > len) return SNAP_EFORMAT;
             uint32_t nd;
-            std::memcpy(&nd, img + off + 32 + 4 * nk, 4);
+            if (!rd(off + 32 + 4 * nk, &nd, 4)) return SNAP_EIO;
             if (nd > nk || off + 36 + 4 * nk + 4ull * nd > len) return SNAP_EFORMAT;
             if (rec[2] != up_page(off + 36 + 4 * nk + 4ull * nd)) return SNAP_EFORMAT;
             uint64_t d = rec[2];
             int64_t last = -1;
             for (uint32_t j = 0; j < nd; ++j) {
                 uint32_t i;
-                std::memcpy(&i, img + off + 36 + 4 * nk + 4ull * j, 4);
+                if (!rd(off + 36 + 4 * nk + 4ull * j, &i, 4)) return SNAP_EIO;
                 if (i >= nk || (int64_t)i <= last) return SNAP_EFORMAT;
                 last = i;
                 const uint64_t L = std::min<uint64_t>(s->C, a.bytes - (uint64_t)i * s->C);
@@ -156,6 +156,14 @@ int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const Im
     }
     if (off > len) return SNAP_EFORMAT;
     return SNAP_OK;
+}
+
+int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes)
+{
+    return walk_records_io(s, [img](uint64_t off, void *dst, uint64_t n) {
+        std::memcpy(dst, img + off, n);
+        return true;
+    }, len, h, hashes);
 }
 
 // ------------------------------------------------------------- set layout
@@ -516,6 +524,7 @@ const char *snap_strerror(int st)
     case SNAP_EMISMATCH: return "image does not match the set";
     case SNAP_EBUSY: return "set busy";
     case SNAP_EBUDGET: return "request exceeds the server budgets";
+    case SNAP_EIO: return "image file I/O error";
     default: return "unknown status";
     }
 }
@@ -676,7 +685,11 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
     rc = quiesce(s, deadline);
     if (rc) return rc;
     const double tq = now_ms();
-    if (!dimg) return ring_checkpoint(s, static_cast<uint8_t *>(host_image), cap, mode, used, t0, tq, deadline);
+    if (!dimg) {
+        ImageIO io;
+        io.mem = static_cast<uint8_t *>(host_image);
+        return ring_checkpoint(s, io, cap, mode, used, t0, tq, deadline);
+    }
 
     const int cur = 1 - s->prev_idx;
     GraphEntry *ge = nullptr;
@@ -722,7 +735,11 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
     rc = quiesce(s, deadline);
     if (rc) return rc;
     const double tq = now_ms();
-    if (!dimg) return ring_restore(s, img, bytes, h, t0, tq, deadline);
+    if (!dimg) {
+        ImageIO io;
+        io.mem = const_cast<uint8_t *>(img);  // read only: restore copies image -> ring
+        return ring_restore(s, io, h, t0, tq, deadline);
+    }
 
     const int cur = 1 - s->prev_idx;
     reset_call(s, dimg, bytes);

@@ -126,6 +126,23 @@ uint8_t *mapped_device_ptr(const void *host);
 void write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n, uint64_t total, uint64_t gen, uint64_t parent);
 int parse_header(const uint8_t *img, uint64_t len, ImageHeader *h);
 int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes);
+// Reads n image bytes at off into dst; false on an I/O failure.
+using ImageReader = std::function<bool(uint64_t off, void *dst, uint64_t n)>;
+int walk_records_io(const snap_set_s *s, const ImageReader &rd, uint64_t len, const ImageHeader &h,
+                    uint32_t *hashes);
+
+// The host end of the ring's pipeline: a pageable image in memory, or an
+// image file (file.cu).  For a file, a failed or short transfer records
+// SNAP_EIO in `err` and later transfers are skipped; zero() is a no-op for
+// a file, whose unwritten ranges read as zero (it is truncated to size first).
+struct ImageIO {
+    uint8_t *mem = nullptr;
+    int fd = -1;
+    std::atomic<int> err{0};
+    void put(uint64_t off, const void *src, uint64_t n);
+    void get(uint64_t off, void *dst, uint64_t n);
+    void zero(uint64_t off, uint64_t n);
+};
 int apply_patch_host(uint8_t *base, uint64_t base_len, const uint8_t *patch, uint64_t patch_len);
 
 // launch shapes (tune.cu)
@@ -133,10 +150,9 @@ void default_shapes(snap_set_s *s);
 TileShape default_hash_shape(int ctas);
 
 // pageable images through the pinned ring (ring.cu)
-int ring_checkpoint(snap_set_s *s, uint8_t *image, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
+int ring_checkpoint(snap_set_s *s, ImageIO &io, uint64_t cap, int mode, uint64_t *used, double t0, double tq,
                     double deadline);
-int ring_restore(snap_set_s *s, const uint8_t *image, uint64_t bytes, const ImageHeader &h, double t0, double tq,
-                 double deadline);
+int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, double tq, double deadline);
 void ring_free(snap_set_s *s);
 int ring_get(snap_set_s *s, Ring **out);  // allocate the ring on first use
 
