@@ -1175,8 +1175,8 @@ def run_file(args, rank, world, local, pg):
       incremental  snap_checkpoint_file(INCREMENTAL) after a 10 % clustered
                    mutation (the patch alone is written), with fsync.
     `value` = state bytes / overlapped checkpoint time (with fsync); the
-    roofline peak is the storage itself: 2 GiB written by 8 threads with
-    pwrite, then fsync, measured in the same run."""
+    roofline peak is the storage itself: 2 GiB written with pwrite by 1 or 8
+    threads (the better), then fsync, measured in the same run."""
     import shutil
     import threading
     import torch
@@ -1280,10 +1280,10 @@ def run_file(args, rank, world, local, pg):
         QS.append(timed(lambda: seq(True)))
         R.append(timed(lambda: s.restore_file(path)))
         kern += s.stats()["kernel_launches"]
+    host = {k: ts[k][lo:hi].cpu().numpy() for k, lo, hi in samples}  # the state the file at `path` holds
     I = [incr() for _ in range(args.steps)]
     clk = clocks.stop()
-    speak = storage_peak()
-    host = {k: ts[k][lo:hi].cpu().numpy() for k, lo, hi in samples}
+    speak = max(storage_peak(threads=1), storage_peak(threads=8))
     for t in ts:
         t.zero_()
     s.restore_file(path)
@@ -1306,7 +1306,8 @@ def run_file(args, rank, world, local, pg):
                            "storage_write_peak_gbs": speak, "d2h_link_gbs": peaks["d2h"]},
                   "roofline": {"bound": "storage", "kernel": "ring checkpoint to file (gather + pwrite + fsync)",
                                "achieved": g(OS), "peak": speak, "unit": "GB/s", "frac": g(OS) / speak,
-                               "note": "peak = 8-thread pwrite + fsync of 2 GiB to the same directory, this run"},
+                               "note": "peak = best of 1- and 8-thread pwrite + fsync of 2 GiB to the same "
+                                       "directory, this run"},
                   "parity": {"file_equals_memory_image": same_header_free, "sampled_chunks": len(samples),
                              "restore_bytes_equal": bool(ok), "verify_mismatches": mism},
                   "clocks": clk, "gpu_launches": kern,

@@ -121,9 +121,13 @@ int snap_checkpoint_file(snap_set s, const char *path, int mode, int flags, uint
     const std::string tmp = std::string(path) + ".tmp";
     const int fd = ::open(tmp.c_str(), O_CREAT | O_TRUNC | O_WRONLY | O_CLOEXEC, 0644);
     if (fd < 0) return SNAP_EIO;
-    // a full image has its final size up front; ranges never written (the
-    // padding) read back as zero
-    if (mode == SNAP_FULL && ::ftruncate(fd, (off_t)s->full_bytes) != 0) rc = SNAP_EIO;
+    // Reserve the image's blocks up front (a patch: its upper bound, trimmed
+    // at the end) so that the workers' concurrent writes land in contiguous
+    // extents instead of interleaving in arrival order; where the file system
+    // cannot preallocate, only set the size.  Ranges never written (the
+    // padding) read back as zero either way.
+    const uint64_t reserve = mode == SNAP_FULL ? s->full_bytes : s->patch_bound;
+    if (::posix_fallocate(fd, 0, (off_t)reserve) != 0 && ::ftruncate(fd, (off_t)reserve) != 0) rc = SNAP_EIO;
     double tq = 0;
     if (rc == SNAP_OK) rc = quiesce(s, deadline);
     tq = now_ms();
