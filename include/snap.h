@@ -60,8 +60,9 @@ typedef enum {
                              (restore needs a compatible target, Sec. 4.4)  */
     SNAP_EBUSY = -8,      /* another call is in progress on this set        */
     SNAP_EBUDGET = -9,    /* request can never fit the server's budgets     */
-    SNAP_EIO = -10        /* opening, reading, writing or renaming an image
+    SNAP_EIO = -10,       /* opening, reading, writing or renaming an image
                              file failed                                    */
+    SNAP_EPEER = -11      /* a coordinated call failed on another rank       */
 } snap_status;
 
 typedef enum { SNAP_FULL = 0, SNAP_INCREMENTAL = 1 } snap_mode;
@@ -338,6 +339,45 @@ SNAP_API int snap_server_submit(snap_server sv, snap_set tenant, int kind, void 
  * latency.  Returns ETIMEDOUT if it is still running. */
 SNAP_API int snap_server_wait(snap_server sv, uint64_t ticket, uint32_t timeout_ms, int *status,
                      snap_stats *st);
+
+/* ----------------------------------------------------------- coordination */
+/* Several processes (one per GPU, each with its own set) take one consistent
+ * checkpoint: every task is locked before any is checkpointed, and the
+ * checkpoint counts only if every task completed it (Sec. 3.1: the lock and
+ * checkpoint actions run for all tasks, and each plugin learns at exit
+ * whether the whole operation succeeded; Sec. 4.4 / Table 3: data-parallel
+ * replicas each store their own copy).  The transport between the ranks is
+ * the caller's: `agree` combines the ranks' statuses (for example an
+ * all-reduce taking the minimum) and returns the global one.
+ *
+ * snap_coordinate runs that two-phase protocol over caller-supplied local
+ * steps (host code only; no GPU needed):
+ *   st = lock();  g = agree(0, st);  if g != OK: return st ? st : EPEER
+ *   st = run();   g = agree(1, st);  if g != OK: abort(); return st ? st : EPEER
+ *   commit();     return OK
+ * lock and run return a status; commit and abort cannot fail.  agree gets
+ * the phase (0 or 1) and the local status and must return the same value on
+ * every rank (a transport failure should be returned as a negative status,
+ * for example ETIMEDOUT).  Any step but agree may be NULL (a no-op). */
+typedef struct {
+    int (*lock)(void *ctx);
+    int (*run)(void *ctx);
+    void (*commit)(void *ctx);
+    void (*abort)(void *ctx);
+    int (*agree)(void *ctx, int phase, int status);
+} snap_coord_ops;
+SNAP_API int snap_coordinate(const snap_coord_ops *ops, void *ctx);
+
+/* snap_checkpoint as one rank of a coordinated checkpoint: lock = quiesce
+ * (plus the argument checks), run = the checkpoint into host_image (pinned or
+ * pageable) without committing, commit = the new hashes and generation become
+ * the base, abort = they are discarded (the image buffer holds a checkpoint
+ * no rank will use).  `agree` and `agree_ctx` as for snap_coordinate.
+ * Returns OK only if every rank completed; EPEER if this rank did and another
+ * did not. */
+typedef int (*snap_agree_fn)(void *ctx, int phase, int status);
+SNAP_API int snap_checkpoint_coordinated(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used,
+                                         snap_agree_fn agree, void *agree_ctx);
 
 #ifdef __cplusplus
 }

@@ -24,8 +24,8 @@ from . import build as _build
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsnap.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGET, EIO = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGET, EIO, EPEER = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11
 FILE_SYNC = 1
 FULL, INCREMENTAL = 0, 1
 REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
@@ -37,7 +37,7 @@ EXPORTS = (
     "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
-    "snap_autotune",
+    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
 
@@ -67,6 +67,16 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+STEP_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p)
+VOID_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
+AGREE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
+
+
+class CoordOps(ctypes.Structure):
+    _fields_ = [("lock", STEP_FN), ("run", STEP_FN), ("commit", VOID_FN), ("abort", VOID_FN),
+                ("agree", AGREE_FN)]
 
 
 class Tuning(ctypes.Structure):
@@ -114,6 +124,8 @@ def _lib():
             "snap_hash_chunks": [vp, u64, u64, vp, vp],
             "snap_hash_chunks_noalloc": [P(vp), P(u64), u32, u64, vp, vp],
             "snap_autotune": [vp, i32, vp, u64, P(Tuning)],
+            "snap_coordinate": [P(CoordOps), vp],
+            "snap_checkpoint_coordinated": [vp, vp, u64, i32, P(u64), AGREE_FN, vp],
             "snap_server_create": [P(vp), u64, u64, P(Opts)],
             "snap_server_destroy": [vp],
             "snap_server_submit": [vp, vp, i32, vp, u64, P(u64)],
@@ -261,6 +273,16 @@ class Set:
         rc = _lib().snap_checkpoint_wait(self.h, timeout_ms, ctypes.byref(used))
         return rc, used.value
 
+    def checkpoint_coordinated(self, image, agree, mode: int = FULL, cap: int | None = None):
+        """One rank of a coordinated checkpoint; `agree(phase, status) ->
+        global status` is the transport (see all_reduce_agree).  Returns
+        (status, image bytes)."""
+        used = ctypes.c_uint64()
+        cb = _agree_callback(agree)
+        rc = _lib().snap_checkpoint_coordinated(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+                                                ctypes.byref(used), cb, None)
+        return rc, used.value
+
     def restore(self, image, nbytes: int | None = None) -> None:
         _check(self.restore_status(image, nbytes), "snap_restore")
 
@@ -374,6 +396,52 @@ def hash_chunks_noalloc(buffers, chunk_bytes: int, out, stream=None) -> int:
         else:
             ptrs[k], sizes[k] = _addr(b), _nbytes(b)
     return _lib().snap_hash_chunks_noalloc(ptrs, sizes, n, chunk_bytes, _addr(out), _stream_handle(stream))
+
+
+def _agree_callback(agree):
+    def f(_ctx, phase, status):
+        try:
+            return int(agree(phase, status))
+        except Exception:  # the transport failed: report it as a failure
+            return ETIMEDOUT
+    return AGREE_FN(f)
+
+
+def coordinate(agree, lock=None, run=None, commit=None, abort=None) -> int:
+    """Run snap_coordinate's two-phase protocol over Python steps: lock() and
+    run() return a status, commit() and abort() nothing, agree(phase, status)
+    returns the global status.  A step that raises counts as ECUDA."""
+    def step(fn):
+        if fn is None:
+            return STEP_FN()
+
+        def f(_ctx):
+            try:
+                return int(fn())
+            except Exception:
+                return ECUDA
+        return STEP_FN(f)
+
+    def vstep(fn):
+        if fn is None:
+            return VOID_FN()
+        return VOID_FN(lambda _ctx: fn())
+
+    ops = CoordOps(step(lock), step(run), vstep(commit), vstep(abort), _agree_callback(agree))
+    return _lib().snap_coordinate(ctypes.byref(ops), None)
+
+
+def all_reduce_agree(group=None):
+    """agree() over torch.distributed: the minimum status of all ranks (every
+    failure is negative), through a CPU tensor (a gloo group)."""
+    import torch
+    import torch.distributed as dist
+
+    def agree(phase, status):
+        t = torch.tensor([status], dtype=torch.int32)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+        return int(t.item())
+    return agree
 
 
 def _stream_handle(stream):

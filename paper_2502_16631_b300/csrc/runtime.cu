@@ -525,6 +525,7 @@ const char *snap_strerror(int st)
     case SNAP_EBUSY: return "set busy";
     case SNAP_EBUDGET: return "request exceeds the server budgets";
     case SNAP_EIO: return "image file I/O error";
+    case SNAP_EPEER: return "the coordinated call failed on another rank";
     default: return "unknown status";
     }
 }
@@ -708,6 +709,110 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
     st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
+}
+
+// One rank of a coordinated checkpoint: the lock / run / commit / abort
+// steps of snap_coordinate over the synchronous checkpoint path.  The run
+// commits like snap_checkpoint; abort puts the previous base back.
+struct CoordCkpt {
+    snap_set_s *s;
+    void *image;
+    uint64_t cap;
+    int mode;
+    uint64_t *used;
+    snap_agree_fn agree;
+    void *agree_ctx;
+    bool busy = false;
+    double t0 = 0, tq = 0, deadline = 0;
+    uint8_t *dimg = nullptr;
+    int prev_idx = 0;
+    bool has_base = false;
+    uint64_t base_gen = 0, next_gen = 0;
+};
+
+static int coord_lock(void *p)
+{
+    CoordCkpt &c = *static_cast<CoordCkpt *>(p);
+    snap_set_s *s = c.s;
+    if (!s || !c.image || ((uintptr_t)c.image & 15u)) return SNAP_EINVAL;
+    if (c.mode != SNAP_FULL && c.mode != SNAP_INCREMENTAL) return SNAP_EINVAL;
+    if (s->busy.exchange(true)) return SNAP_EBUSY;
+    c.busy = true;
+    cudaSetDevice(s->device);
+    c.deadline = c.t0 + s->timeout_ms;
+    int rc = settle(s, c.deadline);
+    if (rc == SNAP_OK) rc = build_layout(s);
+    if (rc) return rc;
+    if (c.mode == SNAP_INCREMENTAL && !s->has_base) return SNAP_ENOBASE;
+    if (c.mode == SNAP_FULL && c.cap < s->full_bytes) return SNAP_EINVAL;
+    if (c.mode == SNAP_INCREMENTAL && c.cap < SNAP_IMG_HEADER_BYTES) return SNAP_EINVAL;
+    c.dimg = mapped_device_ptr(c.image);
+    rc = quiesce(s, c.deadline);
+    c.tq = now_ms();
+    return rc;
+}
+
+static int coord_run(void *p)
+{
+    CoordCkpt &c = *static_cast<CoordCkpt *>(p);
+    snap_set_s *s = c.s;
+    c.prev_idx = s->prev_idx;
+    c.has_base = s->has_base;
+    c.base_gen = s->base_gen;
+    c.next_gen = s->next_gen;
+    if (!c.dimg) {
+        ImageIO io;
+        io.mem = static_cast<uint8_t *>(c.image);
+        return ring_checkpoint(s, io, c.cap, c.mode, c.used, c.t0, c.tq, c.deadline);
+    }
+    const int cur = 1 - s->prev_idx;
+    GraphEntry *ge = nullptr;
+    int rc = checkpoint_graph(s, c.mode, cur, c.dimg, c.cap, false, &ge);
+    if (rc) return rc;
+    s->call_kernels = ge->kernels;
+    rc = cuda_status(cudaGraphLaunch(ge->exec, s->st));
+    if (rc == SNAP_OK) rc = finish(s, c.deadline);
+    if (rc) return rc;
+    snap_stats st{};
+    rc = complete_checkpoint(s, c.mode, cur, static_cast<uint8_t *>(c.image), c.used, st);
+    if (rc) return rc;
+    st.quiesce_ms = c.tq - c.t0;
+    st.kernel_launches = s->call_kernels;
+    st.total_ms = now_ms() - c.t0;
+    st.frozen_ms = st.total_ms;
+    s->last = st;
+    return SNAP_OK;
+}
+
+static void coord_abort(void *p)
+{
+    CoordCkpt &c = *static_cast<CoordCkpt *>(p);
+    c.s->prev_idx = c.prev_idx;
+    c.s->has_base = c.has_base;
+    c.s->base_gen = c.base_gen;
+    c.s->next_gen = c.next_gen;
+}
+
+static int coord_agree(void *p, int phase, int status)
+{
+    CoordCkpt &c = *static_cast<CoordCkpt *>(p);
+    return c.agree(c.agree_ctx, phase, status);
+}
+
+int snap_checkpoint_coordinated(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used,
+                                snap_agree_fn agree, void *agree_ctx)
+{
+    if (!s || !agree) return SNAP_EINVAL;
+    CoordCkpt c{s, host_image, cap, mode, used, agree, agree_ctx};
+    c.t0 = now_ms();
+    snap_coord_ops ops{};
+    ops.lock = coord_lock;
+    ops.run = coord_run;
+    ops.abort = coord_abort;
+    ops.agree = coord_agree;
+    const int rc = coordinate(ops, &c);
+    if (c.busy) s->busy.store(false);
+    return rc;
 }
 
 int snap_restore(const void *host_image, uint64_t bytes, snap_set s)

@@ -184,6 +184,9 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
                      GraphEntry **out);
 int complete_checkpoint(snap_set_s *s, int mode, int cur, uint8_t *host_image, uint64_t *used, snap_stats &st);
 
+// two-phase coordination across ranks (coord.cu)
+int coordinate(const snap_coord_ops &o, void *ctx);
+
 // asynchronous checkpoint resources (async.cu): the shadow and its table
 // (freed with the layout), the background stream and event (freed with the set)
 int async_prepare(snap_set_s *s);

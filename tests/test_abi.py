@@ -38,6 +38,6 @@ def test_library_is_built_for_sm_103a():
 
 
 def test_strerror_names_every_status():
-    for st in range(0, -11, -1):
+    for st in range(0, -12, -1):
         assert snap.strerror(st) != "unknown status"
     assert snap.strerror(-99) == "unknown status"
