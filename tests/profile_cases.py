@@ -4,6 +4,8 @@ under `ncu`; not collected by pytest).
     python tests/profile_cases.py gather [reps]   # 8 x 64 MiB, full checkpoints
     python tests/profile_cases.py scatter [reps]  # 8 x 64 MiB, restores
     python tests/profile_cases.py hash [reps]     # 1 GiB chunk hasher
+    python tests/profile_cases.py cut [reps]      # 8 x 64 MiB, asynchronous checkpoints
+                                                  # (k_shadow_copy is the cut)
 """
 import os
 import sys
@@ -36,7 +38,10 @@ def main():
         img = snap.HostBuffer(s.image_bytes(snap.FULL))
         used = s.checkpoint(img, snap.FULL)
         for _ in range(reps):
-            if op == "gather":
+            if op == "cut":
+                s.checkpoint_async(img, snap.FULL)
+                s.checkpoint_wait()
+            elif op == "gather":
                 s.checkpoint(img, snap.FULL)
             else:
                 s.restore(img, used)
