@@ -193,6 +193,10 @@ def link_peak(torch, nbytes=1 * GiB, reps=5):
             best = max(best, nbytes / (a.elapsed_time(b) * 1e-3) / 1e9)
         out[name] = best
     del d, h
+    import paper_2502_16631_b300 as snap
+    # the ceiling of SM-initiated traffic, which the gather and scatter use
+    out["sm_d2h"] = snap.link_ceiling(0, nbytes, 3)
+    out["sm_h2d"] = snap.link_ceiling(1, nbytes, 3)
     return out
 
 
@@ -446,11 +450,15 @@ def run_snap(args, rank, world, local, pg):
         "roofline": {"bound": "host_link", "kernel": "snap_tiles (OP_GATHER, full checkpoint)",
                      "achieved": achieved, "peak": peaks["d2h"], "unit": "GB/s", "frac": achieved / peaks["d2h"],
                      "peak_source": "pinned cudaMemcpyAsync D2H, 1 GiB, best of 5, measured in this run",
-                     "traffic": traffic_from_profiles("snap_tiles_gather")},
+                     "traffic": traffic_from_profiles("snap_tiles_gather"),
+                     "sm_path_peak": peaks["sm_d2h"], "frac_of_sm_path": achieved / peaks["sm_d2h"]},
         "roofline_restore": {"bound": "host_link", "kernel": "snap_tiles (OP_SCATTER)",
                              "achieved": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9,
                              "peak": peaks["h2d"], "unit": "GB/s",
-                             "frac": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9 / peaks["h2d"]},
+                             "frac": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9 / peaks["h2d"],
+                             "sm_path_peak": peaks["sm_h2d"],
+                             "frac_of_sm_path": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9
+                             / peaks["sm_h2d"]},
         "roofline_hash": {"bound": "hbm", "kernel": "snap_tiles (OP_HASH, incremental hash pass)",
                           "achieved": B / (hash_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                           "frac": B / (hash_ms * 1e-3) / 1e9 / hbm_peak,

@@ -303,6 +303,17 @@ SNAP_API int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_b
 SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *bytes, uint32_t n_buffers,
                                       uint64_t chunk_bytes, uint32_t *hashes, void *stream);
 
+/* Measure the rate at which SM loads and stores move bytes between device
+ * memory and pinned, mapped host memory (direction 0: device to host, 1:
+ * host to device), best of `reps` launches over `bytes` (a multiple of 8 KiB
+ * is used).  This is the ceiling of the gather and scatter kernels, which
+ * move the image with SM accesses; on the measured B300 machines every SM store
+ * form (16-byte stores, TMA bulk stores, plain load/store) reaches the same
+ * rate, below the copy engines'.  Allocates and frees `bytes` of device and
+ * pinned host memory.  device -1 = the current device.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+SNAP_API int snap_link_ceiling(int device, int direction, uint64_t bytes, int reps, double *gbs);
+
 /* ----------------------------------------------------------- autotuning */
 typedef struct {
     uint32_t warps;        /* warps per CTA of the persistent kernel */

@@ -37,7 +37,7 @@ EXPORTS = (
     "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
-    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated",
+    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated", "snap_link_ceiling",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
 
@@ -125,6 +125,7 @@ def _lib():
             "snap_hash_chunks_noalloc": [P(vp), P(u64), u32, u64, vp, vp],
             "snap_autotune": [vp, i32, vp, u64, P(Tuning)],
             "snap_coordinate": [P(CoordOps), vp],
+            "snap_link_ceiling": [i32, i32, u64, i32, P(ctypes.c_double)],
             "snap_checkpoint_coordinated": [vp, vp, u64, i32, P(u64), AGREE_FN, vp],
             "snap_server_create": [P(vp), u64, u64, P(Opts)],
             "snap_server_destroy": [vp],
@@ -405,6 +406,14 @@ def _agree_callback(agree):
         except Exception:  # the transport failed: report it as a failure
             return ETIMEDOUT
     return AGREE_FN(f)
+
+
+def link_ceiling(direction: int = 0, nbytes: int = 1 << 30, reps: int = 3, device: int = -1) -> float:
+    """GB/s that SM loads/stores reach over the host link (0: device to host,
+    1: host to device): the gather and scatter kernels' ceiling."""
+    v = ctypes.c_double()
+    _check(_lib().snap_link_ceiling(device, direction, nbytes, reps, ctypes.byref(v)), "snap_link_ceiling")
+    return v.value
 
 
 def coordinate(agree, lock=None, run=None, commit=None, abort=None) -> int:

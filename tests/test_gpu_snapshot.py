@@ -423,3 +423,15 @@ def test_gpt2_state_full_parity():
     s.restore(img, used)
     for a, b in zip(readback(ts), host):
         assert np.array_equal(a, b)
+
+
+def test_link_ceiling_measures_both_directions():
+    """The SM-path ceiling the gather and scatter are held to: positive in both
+    directions; bad arguments are rejected before anything is allocated."""
+    d2h = snap.link_ceiling(0, 256 * MiB, 1)
+    h2d = snap.link_ceiling(1, 256 * MiB, 1)
+    assert d2h > 1.0 and h2d > 1.0
+    v = __import__("ctypes").c_double()
+    assert snap.lib().snap_link_ceiling(-1, 2, 1 << 20, 1, v) == snap.EINVAL
+    assert snap.lib().snap_link_ceiling(-1, 0, 4096, 1, v) == snap.EINVAL
+    assert snap.lib().snap_link_ceiling(-1, 0, 1 << 20, 0, v) == snap.EINVAL
