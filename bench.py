@@ -54,14 +54,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-bytes", type=int, default=512 * MiB)
     p.add_argument("--workload", default="gpt2",
-                   choices=["gpt2", "random64m", "incr20g", "llama7b", "serving", "async", "lazy", "file"],
+                   choices=["gpt2", "random64m", "incr20g", "llama7b", "serving", "async", "lazy", "file", "hash"],
                    help="gpt2: GPT-2-small training state (default); random64m: 16 random allocations, "
                         "64 MiB; incr20g: 20 GiB incremental at 1/10/50%% dirty with the chunk-size sweep; "
                         "llama7b: 115.8 GB Llama-7B state through the pinned ring; serving: 32 tenants, "
                         "Poisson arrivals; async: GPT-2 state checkpointed asynchronously under a bf16 "
                         "matmul load, against the synchronous call; lazy: GPT-2 state restored weights "
                         "first, time until the weights are usable; file: GPT-2 state checkpointed to and "
-                        "restored from an image file")
+                        "restored from an image file; hash: the chunk hasher alone over 8 GiB")
     p.add_argument("--file-dir", default=None, help="file: directory for the image files (default: the "
                    "system temporary directory)")
     p.add_argument("--load-gemms", type=int, default=0, help="async: matmuls per step (0: about 3x the "
@@ -1329,6 +1329,64 @@ def run_file(args, rank, world, local, pg):
     print(json.dumps(line))
 
 
+def run_hash(args, rank, world, local, pg):
+    """The chunk hasher alone (snap_hash_chunks): CRC-32C of every 64 KiB
+    chunk of an 8 GiB device buffer of random bytes, timed with CUDA events
+    on the launching stream, inputs 64x the L2.  Parity: 256 sampled chunks
+    against the oracle, and the last (ragged) chunk of a 8 GiB - 4,097 B
+    prefix."""
+    import torch
+    import oracle
+    import paper_2502_16631_b300 as snap
+    n = 8 * GiB
+    x = torch.empty(n, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(args.seed)
+    for p in range(0, n, GiB):
+        x[p: p + GiB].copy_(torch.randint(0, 256, (GiB,), dtype=torch.uint8, device="cuda", generator=g))
+    nch = n // UNIT
+    out = torch.empty(nch, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        snap.hash_chunks(x, UNIT, out, stream=st)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    t_end = time.perf_counter() + 1.0  # at least a second, so the clock sampler sees the load
+    while len(times) < args.steps or time.perf_counter() < t_end:
+        a, b = _ev(), _ev()
+        a.record(st)
+        snap.hash_chunks(x, UNIT, out, stream=st)
+        b.record(st)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    got = out.cpu().numpy().view(np.uint32)
+    rng = np.random.default_rng(args.seed)
+    picks = sorted(set(rng.integers(0, nch, 256).tolist()) | {0, nch - 1})
+    ok = all(int(got[c]) == oracle.crc32c(x[c * UNIT: (c + 1) * UNIT].cpu().numpy()) for c in picks)
+    m = n - 4097
+    tail = torch.empty((m + UNIT - 1) // UNIT, dtype=torch.int32, device="cuda")
+    snap.hash_chunks(x, UNIT, tail, nbytes=m, stream=st)
+    torch.cuda.synchronize()
+    last = (m - 1) // UNIT
+    ok &= int(tail[last].cpu().numpy().view(np.uint32)) == oracle.crc32c(x[last * UNIT: m].cpu().numpy())
+    pk = measured_peaks().get("hbm_gbs", 6400.0)
+    best, med = min(times), statistics.median(times)
+    gbs = n / (med * 1e-3) / 1e9
+    line = _line(args, world, gbs, med,
+                 {"workload": "8 GiB device buffer of random bytes, 131,072 chunks of 64 KiB",
+                  "step": "snap_hash_chunks over the whole buffer", "l2": "8 GiB, 64x the L2: no flush"},
+                 {"roofline": {"bound": "hbm", "kernel": "snap_tiles (OP_HASH)", "achieved": gbs, "peak": pk,
+                               "unit": "GB/s", "frac": gbs / pk, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of "
+                               "measured)", "best_gbs": n / (best * 1e-3) / 1e9},
+                  "parity": {"sampled_chunks": len(picks) + 1, "hashes_equal_oracle": bool(ok)},
+                  "clocks": clk, "gpu_launches": len(times), "timed_launches": len(times),
+                  "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    line["metric"] = "chunk hasher GB/s (CRC-32C per 64 KiB chunk)"
+    print(json.dumps(line))
+
+
 def _first_n(sizes, cap):
     tot, n = 0, 0
     for x in sizes:
@@ -1349,7 +1407,7 @@ def main():
     else:
         {"random64m": run_random64m, "incr20g": run_incr20g, "llama7b": run_llama7b,
          "serving": run_serving, "async": run_async, "lazy": run_lazy,
-         "file": run_file}[args.workload](args, rank, world, local, pg)
+         "file": run_file, "hash": run_hash}[args.workload](args, rank, world, local, pg)
     if pg is not None:
         pg.destroy_process_group()
 

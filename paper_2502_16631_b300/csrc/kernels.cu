@@ -32,6 +32,12 @@ __device__ const SliceTables g_slice = make_slice_tables();
 __constant__ Pow8Table c_pow8 = make_pow8_table();
 
 constexpr uint32_t kTableBytes = 4 * 256 * 32 * 4;     // 4 tables x 256 x 32 lanes
+// Shared-window address of the first dynamic shared-memory byte, where the
+// CRC tables start: the 1 KiB below it is reserved per CTA on sm_100-class
+// GPUs.  Folding it into the lookups' immediate offsets saves an add per
+// lookup; the kernel checks it at entry and refuses to run (ERR_SMEM_BASE)
+// if a platform ever places dynamic shared memory elsewhere.
+constexpr uint32_t kTableBase = 1024;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 size_t tile_smem_bytes(const TileShape &sh)
@@ -124,7 +130,10 @@ __device__ __forceinline__ void fence_mbar_init()
 // i.e. each 256-byte row holds one value of two tables for all 32 lanes, so
 // a lane always reads its own bank, and the row offset v * 256 is a single
 // byte-permute of the CRC register.  `lb` is the lane's 32-bit shared
-// address of entry (0, 0); the pair/half part is an immediate offset.
+// address of entry (0, 0); the pair/half part is an immediate offset.  In
+// crc_word one byte-permute builds (v << 8) | (lane * 4) from the CRC
+// register and `l4` = lane * 4, and the table base is part of the immediate,
+// so a lookup is a permute and a load.
 template <int OFF>
 __device__ __forceinline__ uint32_t lds_tab(uint32_t addr)
 {
@@ -132,26 +141,27 @@ __device__ __forceinline__ uint32_t lds_tab(uint32_t addr)
     asm("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
     return v;
 }
-__device__ __forceinline__ uint32_t crc_word(uint32_t crc, uint32_t w, uint32_t lb)
+__device__ __forceinline__ uint32_t crc_word(uint32_t crc, uint32_t w, uint32_t l4)
 {
     const uint32_t x = crc ^ w;
-    // byte i of x, shifted to bits 8..15 (the row offset), others zero
-    const uint32_t a3 = lds_tab<65536 + 128>(lb + __byte_perm(x, 0u, 0x4404u));  // byte 0 -> table 3
-    const uint32_t a2 = lds_tab<65536>(lb + __byte_perm(x, 0u, 0x4414u));        // byte 1 -> table 2
-    const uint32_t a1 = lds_tab<128>(lb + __byte_perm(x, 0u, 0x4424u));          // byte 2 -> table 1
-    const uint32_t a0 = lds_tab<0>(lb + __byte_perm(x, 0u, 0x4434u));            // byte 3 -> table 0
+    // byte 1 of each index = byte i of x (the row), byte 0 = lane * 4 (the
+    // column), bytes 2-3 zero (byte 1 of l4)
+    const uint32_t a3 = lds_tab<kTableBase + 65536 + 128>(__byte_perm(x, l4, 0x5504u));  // byte 0 -> table 3
+    const uint32_t a2 = lds_tab<kTableBase + 65536>(__byte_perm(x, l4, 0x5514u));        // byte 1 -> table 2
+    const uint32_t a1 = lds_tab<kTableBase + 128>(__byte_perm(x, l4, 0x5524u));          // byte 2 -> table 1
+    const uint32_t a0 = lds_tab<kTableBase>(__byte_perm(x, l4, 0x5534u));                // byte 3 -> table 0
     return a0 ^ a1 ^ a2 ^ a3;
 }
 __device__ __forceinline__ uint32_t crc_byte(uint32_t crc, uint32_t b, uint32_t lb)
 {
     return lds_tab<0>(lb + (((crc ^ b) & 0xFFu) << 8)) ^ (crc >> 8);
 }
-__device__ __forceinline__ uint32_t crc_block(uint32_t crc, const uint4 v, uint32_t lb)
+__device__ __forceinline__ uint32_t crc_block(uint32_t crc, const uint4 v, uint32_t l4)
 {
-    crc = crc_word(crc, v.x, lb);
-    crc = crc_word(crc, v.y, lb);
-    crc = crc_word(crc, v.z, lb);
-    return crc_word(crc, v.w, lb);
+    crc = crc_word(crc, v.x, l4);
+    crc = crc_word(crc, v.y, l4);
+    crc = crc_word(crc, v.z, l4);
+    return crc_word(crc, v.w, l4);
 }
 __device__ __forceinline__ uint4 lds128(uint32_t addr)
 {
@@ -192,6 +202,7 @@ struct WarpCtx {
     uint32_t ib, cb, cpar; // next buffer to issue / to consume, its phase parity
     int stages, piece, lane, chains;
     uint32_t lb;           // shared address of this lane's table column
+    uint32_t l4;           // lane * 4 (the column offset inside a table row)
     uint32_t stage_bytes;  // 32 * chains * (piece + 16)
 };
 
@@ -281,7 +292,7 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
         cons_advance(w);
         const uint32_t rd = stage0 + buf * w.stage_bytes + lane * (P + 16u);
 #pragma unroll
-        for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * b), w.lb);
+        for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * b), w.l4);
         __syncwarp();
         if (k + S < nst) issue(k + S);
     }
@@ -328,8 +339,8 @@ __device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, con
         for (uint32_t b = 0; b < BPP; ++b) {
             const uint4 va = lds128(ra + 16u * b);
             const uint4 vb = lds128(rb + 16u * b);
-            ca = crc_block(ca, va, w.lb);
-            cb = crc_block(cb, vb, w.lb);
+            ca = crc_block(ca, va, w.l4);
+            cb = crc_block(cb, vb, w.l4);
         }
         __syncwarp();
         if (k + S < nst) issue(k + S);
@@ -384,9 +395,9 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
             const uint32_t nfull = (phi - plo) >> 4;
             if (nfull == (P >> 4)) {
 #pragma unroll 4
-                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.lb);
+                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.l4);
             } else {
-                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.lb);
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.l4);
             }
             const uint32_t rem = (phi - plo) & 15u;
             if (rem) {
@@ -458,7 +469,7 @@ __device__ bool gather_chunk_int(WarpCtx &w, const uint8_t *src, uint32_t L, uin
                 if (crc != 0u && gap != 0u) crc = gf2_mulmod(crc, gap == 31u * P ? cc.kgap : gf2_x8n(gap, c_pow8));
                 const uint4 *sp = reinterpret_cast<const uint4 *>(sb + (uint32_t)lane * P);
                 const uint32_t nfull = (phi - plo) >> 4;
-                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.lb);
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.l4);
                 const uint32_t rem = (phi - plo) & 15u;
                 if (rem) {
                     const uint8_t *tp = src + plo + (nfull << 4);
@@ -547,6 +558,12 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
     uint64_t *mbars = reinterpret_cast<uint64_t *>(stage_all + (size_t)warps * stages * stage_bytes);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(mbars + warps * stages);
 
+    // the lookups assume the tables at kTableBase; the condition is the same
+    // for every thread, so the whole CTA leaves together
+    if (smem_addr(tables) != kTableBase) {
+        if (threadIdx.x == 0) atomicOr(&kres->err, (unsigned long long)ERR_SMEM_BASE);
+        return;
+    }
     bool need_tables = false;
     for (int j = 0; j < n_jobs; ++j)
         need_tables |= (jobs[j].op == OP_HASH || jobs[j].op == OP_GATHER || jobs[j].op == OP_VERIFY);
@@ -584,6 +601,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
     w.chains = chains;
     w.lane = lane;
     w.lb = smem_addr(tables) + 4u * (uint32_t)lane;
+    w.l4 = 4u * (uint32_t)lane;
     w.stage_bytes = stage_bytes;
 
     for (;;) {

@@ -50,6 +50,7 @@ enum StampId { TS_BEGIN = 0, TS_HASH_END, TS_DIFF_END, TS_COPY_END };
 enum ResultErr : unsigned long long {
     ERR_WAIT_TIMEOUT = 1ull,   // an mbarrier wait passed its deadline
     ERR_BAD_TILE = 2ull,       // a tile resolved outside its allocation table
+    ERR_SMEM_BASE = 4ull,      // dynamic shared memory not where the CRC lookups expect it
 };
 
 // One job: a set of chunk tiles with one operation.
