@@ -42,7 +42,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 
 size_t tile_smem_bytes(const TileShape &sh)
 {
-    return kTableBytes + (size_t)sh.warps * sh.stages * 32 * sh.chains * (sh.piece + 16) +
+    return kTableBytes + (size_t)sh.warps * sh.stages * 32 * sh.chains * sh.piece +
            (size_t)sh.warps * sh.stages * 8 + (kMaxJobs + 1) * 8;
 }
 
@@ -203,7 +203,7 @@ struct WarpCtx {
     int stages, piece, lane, chains;
     uint32_t lb;           // shared address of this lane's table column
     uint32_t l4;           // lane * 4 (the column offset inside a table row)
-    uint32_t stage_bytes;  // 32 * chains * (piece + 16)
+    uint32_t stage_bytes;  // 32 * chains * piece
 };
 
 // The stage ring is walked with incremental counters (no division by the
@@ -236,9 +236,24 @@ __device__ void drain(WarpCtx &w)
 
 // ------------------------------------------- segmented hash (HBM-bound path)
 // Lane l owns bytes [l*s, min((l+1)*s, L)) of the chunk; stage k holds the
-// next P bytes of every lane's segment in slot l (stride P + 16, so the
-// 16-byte reads of 8 consecutive lanes hit 8 different bank groups).  Each
-// cp.async instruction of the warp moves four whole 128-byte lines.
+// next P bytes of every lane's segment in slot l (slot j at j*P).  Inside a
+// slot, 16-byte unit u is stored at unit u ^ swz(j): the 8 lanes of a
+// quarter-warp reading unit u of 8 consecutive slots then hit 8 different
+// 16-byte bank groups, and so do the copies that fill them, with no padding.
+// Each cp.async instruction of the warp moves four whole 128-byte lines.
+template <uint32_t BPP>
+__device__ __forceinline__ uint32_t swz(uint32_t j)
+{
+    if constexpr (BPP == 1) return 0u;
+    else if constexpr (BPP == 2) return (j >> 2) & 1u;
+    else if constexpr (BPP == 4) return (j >> 1) & 3u;
+    else return j & 7u;
+}
+__device__ __forceinline__ uint32_t swz_rt(uint32_t j, uint32_t bpp)
+{
+    return bpp >= 8u ? (j & 7u) : bpp == 4u ? ((j >> 1) & 3u) : bpp == 2u ? ((j >> 2) & 1u) : 0u;
+}
+
 __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t s, uint32_t k)
 {
     const uint32_t buf = issue_advance(w);
@@ -254,7 +269,7 @@ __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32
         const uint32_t seg_hi = j * s + s;
         if (phi > seg_hi) phi = seg_hi;
         if (phi > L) phi = L;
-        if (plo + 16u * b + 16u <= phi) cp_async16(sbs + j * (P + 16u) + 16u * b, src + plo + 16u * b);
+        if (plo + 16u * b + 16u <= phi) cp_async16(sbs + j * P + 16u * (b ^ swz_rt(j, bpp)), src + plo + 16u * b);
     }
     cp_async_arrive(w.mbar + 8 * buf);
 }
@@ -272,16 +287,19 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
     const uint32_t nst = s / P;
     const uint32_t jl = lane / BPP, bl = lane % BPP;
     const uint8_t *sp0 = src + jl * s + 16u * bl;
-    const uint32_t d0 = jl * (P + 16u) + 16u * bl;
     const uint32_t stage0 = smem_addr(w.stage);
     const uint32_t S = (uint32_t)w.stages;
+    const uint32_t rsw = swz<BPP>(lane);
     uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
 
     auto issue = [&](uint32_t k) {
         const uint32_t buf = issue_advance(w);
         const uint32_t sbs = stage0 + buf * w.stage_bytes;
 #pragma unroll
-        for (uint32_t m = 0; m < BPP; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
+        for (uint32_t m = 0; m < BPP; ++m) {
+            const uint32_t j = jl + m * PPI;
+            cp_async16(sbs + j * P + 16u * (bl ^ swz<BPP>(j)), sp0 + m * PPI * s + k * P);
+        }
         cp_async_arrive(w.mbar + 8 * buf);
     };
     const uint32_t pre = nst < S ? nst : S;
@@ -290,9 +308,9 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
         const uint32_t buf = w.cb;
         if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
         cons_advance(w);
-        const uint32_t rd = stage0 + buf * w.stage_bytes + lane * (P + 16u);
+        const uint32_t rd = stage0 + buf * w.stage_bytes + lane * P;
 #pragma unroll
-        for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * b), w.l4);
+        for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * (b ^ rsw)), w.l4);
         __syncwarp();
         if (k + S < nst) issue(k + S);
     }
@@ -315,16 +333,19 @@ __device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, con
     const uint32_t nst = s / P;
     const uint32_t jl = lane / BPP, bl = lane % BPP;
     const uint8_t *sp0 = src + jl * s + 16u * bl;
-    const uint32_t d0 = jl * (P + 16u) + 16u * bl;
     const uint32_t stage0 = smem_addr(w.stage);
     const uint32_t S = (uint32_t)w.stages;
+    const uint32_t rsw = swz<BPP>(lane);  // = swz(lane + 32)
     uint32_t ca = lane == 0 ? 0xFFFFFFFFu : 0u, cb = 0u;
 
     auto issue = [&](uint32_t k) {
         const uint32_t buf = issue_advance(w);
         const uint32_t sbs = stage0 + buf * w.stage_bytes;
 #pragma unroll
-        for (uint32_t m = 0; m < NI; ++m) cp_async16(sbs + d0 + m * PPI * (P + 16u), sp0 + m * PPI * s + k * P);
+        for (uint32_t m = 0; m < NI; ++m) {
+            const uint32_t j = jl + m * PPI;
+            cp_async16(sbs + j * P + 16u * (bl ^ swz<BPP>(j)), sp0 + m * PPI * s + k * P);
+        }
         cp_async_arrive(w.mbar + 8 * buf);
     };
     const uint32_t pre = nst < S ? nst : S;
@@ -333,12 +354,12 @@ __device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, con
         const uint32_t buf = w.cb;
         if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
         cons_advance(w);
-        const uint32_t ra = stage0 + buf * w.stage_bytes + lane * (P + 16u);
-        const uint32_t rb = ra + 32u * (P + 16u);
+        const uint32_t ra = stage0 + buf * w.stage_bytes + lane * P;
+        const uint32_t rb = ra + 32u * P;
 #pragma unroll
         for (uint32_t b = 0; b < BPP; ++b) {
-            const uint4 va = lds128(ra + 16u * b);
-            const uint4 vb = lds128(rb + 16u * b);
+            const uint4 va = lds128(ra + 16u * (b ^ rsw));
+            const uint4 vb = lds128(rb + 16u * (b ^ rsw));
             ca = crc_block(ca, va, w.l4);
             cb = crc_block(cb, vb, w.l4);
         }
@@ -387,17 +408,17 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
         const uint32_t buf = w.cb;
         if (!mbar_wait(w.mbar + 8 * buf, w.cpar)) return false;
         cons_advance(w);
-        const uint8_t *sb = w.stage + buf * w.stage_bytes;
         const uint32_t plo = lo + k * P;
         if (plo < hi) {
             const uint32_t phi = plo + P < hi ? plo + P : hi;
-            const uint4 *sp = reinterpret_cast<const uint4 *>(sb + lane * (P + 16u));
+            const uint32_t rd = smem_addr(w.stage + buf * w.stage_bytes) + (uint32_t)lane * P;
+            const uint32_t rsw = swz_rt((uint32_t)lane, P >> 4);
             const uint32_t nfull = (phi - plo) >> 4;
             if (nfull == (P >> 4)) {
 #pragma unroll 4
-                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, sp[b], w.l4);
+                for (uint32_t b = 0; b < (P >> 4); ++b) crc = crc_block(crc, lds128(rd + 16u * (b ^ rsw)), w.l4);
             } else {
-                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, sp[b], w.l4);
+                for (uint32_t b = 0; b < nfull; ++b) crc = crc_block(crc, lds128(rd + 16u * (b ^ rsw)), w.l4);
             }
             const uint32_t rem = (phi - plo) & 15u;
             if (rem) {
@@ -553,7 +574,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t stage_bytes = 32u * (uint32_t)chains * (uint32_t)(piece + 16);
+    const uint32_t stage_bytes = 32u * (uint32_t)chains * (uint32_t)piece;
     uint8_t *stage_all = smem + kTableBytes;
     uint64_t *mbars = reinterpret_cast<uint64_t *>(stage_all + (size_t)warps * stages * stage_bytes);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(mbars + warps * stages);
