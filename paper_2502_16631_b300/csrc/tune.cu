@@ -131,7 +131,7 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
     if (s->n_chunks == 0) return SNAP_EINVAL;
     const int kind = mode == SNAP_FULL ? SHAPE_GATHER : SHAPE_HASH;
     const uint32_t op = mode == SNAP_FULL ? OP_GATHER : OP_HASH;
-    static const int warps_h[] = {8, 16, 24, 32};
+    static const int warps_h[] = {8, 12, 16, 20, 24, 32};
     static const int warps_g[] = {2, 4, 8};
     static const int stages_c[] = {2, 3, 4};
     static const int piece_h[] = {32, 64, 128};
@@ -144,7 +144,7 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
     TileShape best = s->shape[kind];
     double best_ms = 1e30;
     std::vector<uint32_t> ref, cur;
-    const int nwl = mode == SNAP_FULL ? 3 : 4;
+    const int nwl = mode == SNAP_FULL ? 3 : 6;
     for (int a = 0; a < nwl; ++a)
         for (int b = 0; b < 3; ++b)
             for (int c = 0; c < np; ++c)
