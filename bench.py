@@ -280,9 +280,21 @@ def cpu_baseline(sample, args, seconds_target=15.0):
         if time.perf_counter() - t0 > seconds_target or n >= 50:
             break
     dt = (time.perf_counter() - t0) / n
+    # the same step on one thread (a few seconds)
+    oracle.set_threads(1)
+    step1, _ = oracle_step_sample(sample, args.dirty, args.seed)
+    t1 = time.perf_counter()
+    n1 = 0
+    while n1 < 1 or (time.perf_counter() - t1 < seconds_target / 3 and n1 < 10):
+        step1()
+        n1 += 1
+    dt1 = (time.perf_counter() - t1) / n1
+    oracle.set_threads(cores)
     return {"value": 4 * nb / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "value_1_thread": 4 * nb / dt1 / 1e9,
             "sample": "first %d GPT-2-state allocations (%d B), %d steps of full+incremental+verify+restore, "
-                      "%.1f s" % (len(sample), nb, n, dt * n)}
+                      "%.1f s on %d cores; %d steps on 1 thread; host copies of the state, so no device "
+                      "read-back is timed" % (len(sample), nb, n, dt * n, cores, n1)}
 
 
 def sample_allocations(sizes, cap_bytes, seed):
@@ -475,6 +487,10 @@ def run_snap(args, rank, world, local, pg):
             "hash_ms": hash_ms, "diff_ms": statistics.mean(per["diff"]),
             "dirty_gather_ms": statistics.mean(per["dirty_gather"]),
             "gather_kernel_ms": gather_ms, "scatter_kernel_ms": statistics.mean(per["scatter_kernel"]),
+            # per call over the timed steps: median and standard deviation (ms)
+            "call_ms": {k: {"median": statistics.median(per[k]),
+                            "std": statistics.stdev(per[k]) if len(per[k]) > 1 else 0.0}
+                        for k in ("full", "incr", "verify", "restore")},
         },
         "link_peak_gbs": peaks,
         "e2e": {"value": total_bytes / (host_ms_max * 1e-3) / 1e9, "unit": "GB/s",
