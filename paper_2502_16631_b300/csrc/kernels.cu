@@ -644,7 +644,9 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
         while (j + 1 < n_jobs && prefix[j + 1] <= t) ++j;
         const Job &jb = jobs[j];
         const unsigned long long tt = t - prefix[j];
-        const uint64_t chunk = jb.tile_list ? (uint64_t)jb.tile_list[tt] : jb.tile_begin + tt;
+        // a list job may start at a device-side position of its list
+        const unsigned long long toff = jb.tile_off_dev ? *jb.tile_off_dev : 0ull;
+        const uint64_t chunk = jb.tile_list ? (uint64_t)jb.tile_list[tt + toff] : jb.tile_begin + tt;
         const uint64_t k = find_alloc(jb.allocs, jb.n_allocs, chunk);
         const AllocDesc ad = jb.allocs[k];
         const uint64_t C = jb.chunk_bytes;
@@ -706,11 +708,16 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
                 break;
             }
             if (jb.cap_exceeded && *reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) break;
-            // IMAGE: the chunk's slot in the patch (dirty rank window_off + tt);
+            // IMAGE: the chunk's slot in the patch (dirty rank window_off +
+            // toff + tt, which must fall in its allocation's dirty range);
             // PACKED: slot tt of a ring window of C-byte slots
-            uint8_t *dst = jb.layout == LAYOUT_IMAGE
-                               ? jb.host + jb.patch_data[k] + (jb.window_off + tt - jb.dstart[k]) * C
-                               : jb.host + tt * C;
+            const unsigned long long rank = jb.window_off + toff + tt;
+            if (jb.layout == LAYOUT_IMAGE && (rank < jb.dstart[k] || rank >= jb.dstart[k + 1])) {
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+                break;
+            }
+            uint8_t *dst = jb.layout == LAYOUT_IMAGE ? jb.host + jb.patch_data[k] + (rank - jb.dstart[k]) * C
+                                                     : jb.host + tt * C;
             ok = gather_chunk_int(w, dsrc, L, (uint32_t)C, false, dst, cc, h);
             if (ok && (L & 4095u)) warp_zero(dst + L, up_page(L) - L, lane);
             break;

@@ -112,12 +112,15 @@ cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_
 }
 
 // ----------------------------------------------------------- diff + compact
-// dirty(c) = cur[c] != prev[c]
-__global__ void k_diff_count(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ prev, uint64_t n,
-                             unsigned int *blockcnt)
+// dirty(c) = cur[c] != prev[c], over the chunk range [c0, c0 + n).  The
+// range form lets an incremental checkpoint diff one group of allocations
+// at a time; the dirty list stays globally ascending because the groups
+// are diffed in chunk order, each continuing the running count.
+__global__ void k_diff_count(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ prev, uint64_t c0,
+                             uint64_t n, unsigned int *blockcnt)
 {
-    const uint64_t c = (uint64_t)blockIdx.x * kDiffBlock + threadIdx.x;
-    const int d = c < n && cur[c] != prev[c];
+    const uint64_t i = (uint64_t)blockIdx.x * kDiffBlock + threadIdx.x;
+    const int d = i < n && cur[c0 + i] != prev[c0 + i];
     const int cnt = __syncthreads_count(d);
     if (threadIdx.x == 0) blockcnt[blockIdx.x] = (unsigned)cnt;
 }
@@ -151,9 +154,15 @@ __device__ unsigned long long block_exscan(unsigned long long v, unsigned long l
     return before;
 }
 
-__global__ void k_diff_scan(const unsigned int *blockcnt, uint64_t nb, unsigned long long *blockoff, Result *res)
+// `run` holds the dirty entries listed so far (0 for a whole-state diff);
+// the range's entries go after them, and gbeg / gcnt (optional) receive the
+// range's first list position and count.
+__global__ void k_diff_scan(const unsigned int *blockcnt, uint64_t nb, unsigned long long *blockoff,
+                            unsigned long long *run, unsigned long long *gbeg, unsigned long long *gcnt)
 {
-    unsigned long long carry = 0;
+    const unsigned long long carry0 = *run;
+    __syncthreads();  // every thread has read `run` before thread 0 rewrites it
+    unsigned long long carry = carry0;
     for (uint64_t base = 0; base < nb; base += kDiffBlock) {
         const uint64_t b = base + threadIdx.x;
         const unsigned long long v = b < nb ? blockcnt[b] : 0ull;
@@ -162,16 +171,21 @@ __global__ void k_diff_scan(const unsigned int *blockcnt, uint64_t nb, unsigned 
         if (b < nb) blockoff[b] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) res->n_dirty = carry;
+    if (threadIdx.x == 0) {
+        if (gbeg) *gbeg = carry0;
+        if (gcnt) *gcnt = carry - carry0;
+        *run = carry;
+    }
 }
 
-__global__ void k_diff_list(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ prev, uint64_t n,
-                            const unsigned long long *blockoff, uint32_t *dlist)
+__global__ void k_diff_list(const uint32_t *__restrict__ cur, const uint32_t *__restrict__ prev, uint64_t c0,
+                            uint64_t n, const unsigned long long *blockoff, uint32_t *dlist)
 {
     __shared__ unsigned int wcnt[32];
-    const uint64_t c = (uint64_t)blockIdx.x * kDiffBlock + threadIdx.x;
+    const uint64_t i = (uint64_t)blockIdx.x * kDiffBlock + threadIdx.x;
+    const uint64_t c = c0 + i;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool d = c < n && cur[c] != prev[c];
+    const bool d = i < n && cur[c] != prev[c];
     const unsigned int ball = __ballot_sync(0xFFFFFFFFu, d);
     if (lane == 0) wcnt[warp] = __popc(ball);
     __syncthreads();
@@ -181,14 +195,23 @@ __global__ void k_diff_list(const uint32_t *__restrict__ cur, const uint32_t *__
     if (d) dlist[blockoff[blockIdx.x] + rank] = (uint32_t)c;
 }
 
+cudaError_t launch_diff_range(const uint32_t *cur, const uint32_t *prev, uint64_t c0, uint64_t n,
+                              unsigned int *blockcnt, unsigned long long *blockoff, uint32_t *dlist,
+                              unsigned long long *run, unsigned long long *gbeg, unsigned long long *gcnt,
+                              cudaStream_t st)
+{
+    const uint64_t nb = (n + kDiffBlock - 1) / kDiffBlock;
+    if (nb) k_diff_count<<<(unsigned)nb, kDiffBlock, 0, st>>>(cur, prev, c0, n, blockcnt);
+    k_diff_scan<<<1, kDiffBlock, 0, st>>>(blockcnt, nb, blockoff, run, gbeg, gcnt);
+    if (nb) k_diff_list<<<(unsigned)nb, kDiffBlock, 0, st>>>(cur, prev, c0, n, blockoff, dlist);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diff(const uint32_t *cur, const uint32_t *prev, uint64_t n, unsigned int *blockcnt,
                         unsigned long long *blockoff, uint32_t *dlist, Result *res, cudaStream_t st)
 {
-    const uint64_t nb = (n + kDiffBlock - 1) / kDiffBlock;
-    if (nb) k_diff_count<<<(unsigned)nb, kDiffBlock, 0, st>>>(cur, prev, n, blockcnt);
-    k_diff_scan<<<1, kDiffBlock, 0, st>>>(blockcnt, nb, blockoff, res);
-    if (nb) k_diff_list<<<(unsigned)nb, kDiffBlock, 0, st>>>(cur, prev, n, blockoff, dlist);
-    return cudaGetLastError();
+    // res->n_dirty is zero at the start of every launch sequence
+    return launch_diff_range(cur, prev, 0, n, blockcnt, blockoff, dlist, &res->n_dirty, nullptr, nullptr, st);
 }
 
 // ------------------------------------------------------------ patch layout
@@ -206,17 +229,23 @@ __device__ uint64_t lower_bound_u32(const uint32_t *a, uint64_t n, uint64_t key)
     return lo;
 }
 
-__global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C,
+// Allocations [a0, a0 + na); `run_off` carries the patch offset where
+// allocation a0's record starts from the previous range (a0 == 0 starts
+// after the 64-byte header).  The dirty list must already hold every dirty
+// chunk of allocations < a0 + na, and no later one.
+__global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t a0, uint64_t na, uint64_t C,
                                const uint32_t *__restrict__ dlist, uint64_t *patch_rec, uint64_t *patch_data,
-                               uint64_t *dstart, const CallParams *cp, Result *res)
+                               uint64_t *dstart, const CallParams *cp, Result *res, unsigned long long *run_off)
 {
     const uint64_t cap = cp->cap;
     const unsigned long long nd_all = res->n_dirty;
-    unsigned long long carry = 64;
-    for (uint64_t base = 0; base < n_allocs; base += kDiffBlock) {
+    unsigned long long carry = a0 == 0 ? 64ull : *run_off;
+    __syncthreads();  // every thread has read `run_off` before thread 0 rewrites it
+    const uint64_t a1 = a0 + na;
+    for (uint64_t base = a0; base < a1; base += kDiffBlock) {
         const uint64_t k = base + threadIdx.x;
         unsigned long long R = 0, meta_pad = 0, ds = 0;
-        if (k < n_allocs) {
+        if (k < a1) {
             const AllocDesc a = allocs[k];
             const uint64_t nk = (a.bytes + C - 1) / C;
             ds = lower_bound_u32(dlist, nd_all, a.chunk0);
@@ -233,7 +262,7 @@ __global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t n_
         }
         unsigned long long tot;
         const unsigned long long ex = block_exscan(R, &tot);
-        if (k < n_allocs) {
+        if (k < a1) {
             const unsigned long long rec = carry + ex;
             patch_rec[k] = rec;
             patch_data[k] = rec + meta_pad;
@@ -242,30 +271,42 @@ __global__ void k_patch_layout(const AllocDesc *__restrict__ allocs, uint64_t n_
         carry += tot;
     }
     if (threadIdx.x == 0) {
-        dstart[n_allocs] = nd_all;
+        dstart[a1] = nd_all;
+        *run_off = carry;
         res->patch_bytes = carry;
-        res->cap_exceeded = carry > cap ? 1ull : 0ull;
+        if (carry > cap) res->cap_exceeded = 1ull;
     }
+}
+
+cudaError_t launch_patch_layout_range(const AllocDesc *allocs, uint64_t a0, uint64_t na, uint64_t C,
+                                      const uint32_t *dlist, uint64_t *patch_rec, uint64_t *patch_data,
+                                      uint64_t *dstart, const CallParams *cp, Result *res,
+                                      unsigned long long *run_off, cudaStream_t st)
+{
+    k_patch_layout<<<1, kDiffBlock, 0, st>>>(allocs, a0, na, C, dlist, patch_rec, patch_data, dstart, cp, res,
+                                             run_off);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, const uint32_t *dlist,
                                 uint64_t *patch_rec, uint64_t *patch_data, uint64_t *dstart, const CallParams *cp,
                                 Result *res, cudaStream_t st)
 {
-    k_patch_layout<<<1, kDiffBlock, 0, st>>>(allocs, n_allocs, C, dlist, patch_rec, patch_data, dstart, cp, res);
-    return cudaGetLastError();
+    // res->pad[0] serves as the running offset of a whole-state layout
+    return launch_patch_layout_range(allocs, 0, n_allocs, C, dlist, patch_rec, patch_data, dstart, cp, res,
+                                     &res->pad[0], st);
 }
 
 // Block k writes allocation k's patch metadata: record header, all new
 // hashes, the dirty count, the ascending dirty index list and zero padding.
-__global__ void k_patch_meta(const AllocDesc *__restrict__ allocs, uint64_t n_allocs, uint64_t C,
+__global__ void k_patch_meta(const AllocDesc *__restrict__ allocs, uint64_t a0, uint64_t n_allocs, uint64_t C,
                              const uint32_t *__restrict__ cur, const uint32_t *__restrict__ dlist,
                              const uint64_t *__restrict__ patch_rec, const uint64_t *__restrict__ patch_data,
                              const uint64_t *__restrict__ dstart, const Result *res, const CallParams *cp)
 {
     if (res->cap_exceeded) return;
     uint8_t *image = cp->image;
-    const uint64_t k = blockIdx.x;
+    const uint64_t k = a0 + blockIdx.x;
     if (k >= n_allocs) return;
     const AllocDesc a = allocs[k];
     const uint64_t nk = (a.bytes + C - 1) / C;
@@ -288,14 +329,22 @@ __global__ void k_patch_meta(const AllocDesc *__restrict__ allocs, uint64_t n_al
     for (uint64_t q = threadIdx.x; q < nz; q += blockDim.x) z[q] = 0u;
 }
 
+cudaError_t launch_patch_meta_range(const AllocDesc *allocs, uint64_t a0, uint64_t na, uint64_t C,
+                                    const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
+                                    const uint64_t *patch_data, const uint64_t *dstart, const Result *res,
+                                    const CallParams *cp, cudaStream_t st)
+{
+    if (na == 0) return cudaSuccess;
+    k_patch_meta<<<(unsigned)na, 256, 0, st>>>(allocs, a0, a0 + na, C, cur, dlist, patch_rec, patch_data, dstart,
+                                               res, cp);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, const uint32_t *cur,
                               const uint32_t *dlist, const uint64_t *patch_rec, const uint64_t *patch_data,
                               const uint64_t *dstart, const Result *res, const CallParams *cp, cudaStream_t st)
 {
-    if (n_allocs == 0) return cudaSuccess;
-    k_patch_meta<<<(unsigned)n_allocs, 256, 0, st>>>(allocs, n_allocs, C, cur, dlist, patch_rec, patch_data, dstart,
-                                                     res, cp);
-    return cudaGetLastError();
+    return launch_patch_meta_range(allocs, 0, n_allocs, C, cur, dlist, patch_rec, patch_data, dstart, res, cp, st);
 }
 
 }  // namespace snapk

@@ -193,6 +193,33 @@ static void free_device(snap_set_s *s)
     lazy_free_layout(s);
 }
 
+// Groups of whole allocations, in registration order, of about equal bytes
+// and at least 64 MiB each, for the pipelined incremental checkpoint (one
+// group: no pipeline).
+static void plan_groups(snap_set_s *s)
+{
+    const uint64_t kGroupBytes = 64ull << 20;
+    const size_t n = s->desc.size();
+    const int G = (int)std::min<uint64_t>((uint64_t)kMaxGroups, s->total_bytes / kGroupBytes);
+    int g = 0;
+    s->gal[0] = 0;
+    s->gch[0] = 0;
+    if (G >= 2) {
+        uint64_t cum = 0;
+        for (size_t k = 0; k + 1 < n; ++k) {
+            cum += s->desc[k].bytes;
+            if (g + 1 < G && cum * (uint64_t)G >= (uint64_t)(g + 1) * s->total_bytes) {
+                ++g;
+                s->gal[g] = k + 1;
+                s->gch[g] = s->desc[k + 1].chunk0;
+            }
+        }
+    }
+    s->n_groups = g + 1;
+    s->gal[s->n_groups] = n;
+    s->gch[s->n_groups] = s->n_chunks;
+}
+
 int build_layout(snap_set_s *s)
 {
     if (!s->layout_dirty) return SNAP_OK;
@@ -219,6 +246,7 @@ int build_layout(snap_set_s *s)
     }
     s->n_chunks = chunk;
     s->total_bytes = state;
+    plan_groups(s);
     s->full_bytes = off;
     if (chunk > 0xFFFFFFFFull) return SNAP_EINVAL;  // dirty lists hold u32 chunk indices
     // patch upper bound: full image + per allocation the dirty count, index list and a page
@@ -408,6 +436,88 @@ int async_ctas(const snap_set_s *s)
     return std::max(1, std::min(c, s->sms));
 }
 
+// Pipelined incremental checkpoint.  The hash pass (HBM-bound) of allocation
+// group g+1 runs on all but kPipeGatherCtas SMs while the dirty chunks of
+// group g cross the link (link-bound) on the others: a second stream hashes
+// the groups back to back, and the library stream takes each finished group
+// through diff, layout, metadata and gather.  Groups are whole allocations
+// in registration order, so the dirty list stays ascending and every offset
+// of the patch is the one the whole-state layout gives: the bytes are those
+// of the unpipelined sequence.  Used only when the image capacity covers the
+// largest possible patch, because a group's bytes are written before later
+// groups are laid out.
+static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEntry **out)
+{
+    const int G = s->n_groups;
+    if (!s->st_pipe) {
+        const cudaError_t e = cudaStreamCreateWithFlags(&s->st_pipe, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            s->st_pipe = nullptr;
+            return cuda_status(e);
+        }
+    }
+    for (int i = 0; i < G + 2; ++i)
+        if (!s->ev_pipe[i]) {
+            const cudaError_t e = cudaEventCreateWithFlags(&s->ev_pipe[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    CallBlock &cb = *s->h_cb;
+    for (int g = 0; g < G; ++g) {
+        Job jh = base_job(s, OP_HASH);
+        jh.tile_begin = s->gch[g];
+        jh.n_tiles = s->gch[g + 1] - s->gch[g];
+        jh.hash_out = s->d_hash[cur];
+        cb.jobs[g] = jh;
+        Job jg = base_job(s, OP_GATHER_DIRTY);
+        jg.host = dimg;
+        jg.tile_list = s->d_dlist;
+        jg.tile_off_dev = &s->d_cb->gbeg[g];
+        jg.n_tiles_dev = &s->d_cb->gcnt[g];
+        jg.patch_data = s->d_patch_data;
+        jg.dstart = s->d_dstart;
+        jg.cap_exceeded = &s->d_cb->res.cap_exceeded;
+        cb.jobs[G + g] = jg;
+    }
+    TileShape shh = s->shape[SHAPE_HASH], shg = s->shape[SHAPE_GATHER];
+    shh.ctas = std::max(1, s->sms - kPipeGatherCtas);
+    shg.ctas = kPipeGatherCtas;
+    const CombineConsts cch = make_combine_consts(s->C, shh.piece);
+    const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
+    const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
+    CallBlock *d = s->d_cb;
+    return get_graph(s, GK_INCR_PIPE, cur, [&](cudaStream_t q) {
+        cudaStream_t h = s->st_pipe;
+        cudaError_t e = enqueue_prologue(s, q);
+        // fork the hash stream off the capture
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[0], q);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h, s->ev_pipe[0], 0);
+        if (e == cudaSuccess) e = launch_stamp(&d->res, TS_DIFF_END, q);  // copy_ms spans the whole pipeline
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            if (s->gch[g + 1] > s->gch[g])
+                e = launch_tiles(d->jobs + g, 1, &d->cursor[g], cch, shh, &d->res, h);
+            if (e == cudaSuccess && g == G - 1) e = launch_stamp(&d->res, TS_HASH_END, h);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[1 + g], h);
+        }
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            const uint64_t a0 = s->gal[g], na = s->gal[g + 1] - s->gal[g];
+            e = cudaStreamWaitEvent(q, s->ev_pipe[1 + g], 0);
+            if (e == cudaSuccess)
+                e = launch_diff_range(curp, prevp, s->gch[g], s->gch[g + 1] - s->gch[g], s->d_blockcnt,
+                                      s->d_blockoff, s->d_dlist, &d->res.n_dirty, &d->gbeg[g], &d->gcnt[g], q);
+            if (e == cudaSuccess)
+                e = launch_patch_layout_range(s->d_allocs, a0, na, s->C, s->d_dlist, s->d_patch_rec,
+                                              s->d_patch_data, s->d_dstart, &d->cp, &d->res, &d->run_off, q);
+            if (e == cudaSuccess)
+                e = launch_patch_meta_range(s->d_allocs, a0, na, s->C, curp, s->d_dlist, s->d_patch_rec,
+                                            s->d_patch_data, s->d_dstart, &d->res, &d->cp, q);
+            if (e == cudaSuccess)
+                e = launch_tiles(d->jobs + G + g, 1, &d->cursor[G + g], ccg, shg, &d->res, q);
+        }
+        if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+        return e;
+    }, out);
+}
+
 // Fill the call block of a checkpoint into the mapped image `dimg` and get
 // (capturing it on first use) its graph: FULL = records + gather of every
 // chunk with its CRC; INCREMENTAL = hash, diff against the committed table,
@@ -437,6 +547,7 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
             return e;
         }, out);
     }
+    if (!from_shadow && s->n_groups >= 2 && cap >= s->patch_bound) return pipelined_incremental(s, cur, dimg, out);
     Job jh = base_job(s, OP_HASH);
     jh.allocs = allocs;
     jh.hash_out = s->d_hash[cur];
@@ -603,6 +714,9 @@ int snap_set_destroy(snap_set s)
     ring_free(s);
     async_free(s);
     lazy_free(s);
+    for (auto &ev : s->ev_pipe)
+        if (ev) cudaEventDestroy(ev);
+    if (s->st_pipe) cudaStreamDestroy(s->st_pipe);
     cudaFree(s->d_cb);
     cudaFreeHost(s->h_cb);
     cudaFreeHost(s->h_res);

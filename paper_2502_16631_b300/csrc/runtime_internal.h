@@ -19,17 +19,27 @@ struct ImageHeader {
     uint64_t chunk_bytes, n_allocs, total, generation, parent;
 };
 
+// A pipelined incremental checkpoint splits the allocations into at most
+// this many groups (whole allocations, in registration order).
+constexpr int kMaxGroups = 8;
+// CTAs that gather dirty chunks while the other SMs hash the next group: the
+// device-to-host link saturates with 8 gather CTAs on B300.
+constexpr int kPipeGatherCtas = 8;
+
 // Everything one launch sequence needs that changes from call to call; the
 // host fills a pinned copy and the captured graph's first node copies it in.
 struct CallBlock {
-    unsigned long long cursor[4];  // tile cursors of the sequence's launches
+    unsigned long long cursor[2 * kMaxGroups + 2];  // tile cursors of the sequence's launches
+    unsigned long long gbeg[kMaxGroups];            // pipelined incremental: each group's
+    unsigned long long gcnt[kMaxGroups];            //   dirty-list range
+    unsigned long long run_off;                     //   and the running patch offset
     Result res;
     CallParams cp;
     Job jobs[kMaxJobs];
 };
 
 enum EventId { EV_BEGIN = 0, EV_HASH_END, EV_DIFF_END, EV_COPY_END, EV_END, EV_COUNT };
-enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY, GK_ASYNC_FULL, GK_ASYNC_INCR };
+enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY, GK_ASYNC_FULL, GK_ASYNC_INCR, GK_INCR_PIPE };
 enum ShapeKind { SHAPE_GATHER = 0, SHAPE_HASH, SHAPE_SCATTER, SHAPE_COUNT };
 
 struct GraphEntry {
@@ -78,6 +88,13 @@ struct snap_set_s {
     bool has_base = false;
     uint64_t base_gen = 0;
     uint64_t next_gen = 0;
+
+    // pipelined incremental: allocation groups [gal[g], gal[g+1]) covering
+    // chunks [gch[g], gch[g+1]); a second stream and its fork/join events
+    int n_groups = 0;
+    uint64_t gal[snapk::kMaxGroups + 1] = {}, gch[snapk::kMaxGroups + 1] = {};
+    cudaStream_t st_pipe = nullptr;
+    cudaEvent_t ev_pipe[snapk::kMaxGroups + 2] = {};
 
     std::vector<snapk::GraphEntry> graphs;
     snapk::TileShape shape[snapk::SHAPE_COUNT];

@@ -62,6 +62,7 @@ struct Job {
     uint64_t n_tiles;              // identity tiles: count
     const uint32_t *tile_list;     // list tiles (ascending global chunks), or null
     const unsigned long long *n_tiles_dev;  // list tiles: count on the device
+    const unsigned long long *tile_off_dev; // list tiles: first list entry, on the device (or null: 0)
     uint8_t *host;                 // device-visible address of the host image / window
     uint64_t window_off;           // LAYOUT_PACKED
     uint32_t op;                   // JobOp
@@ -125,6 +126,22 @@ cudaError_t launch_diff(const uint32_t *cur, const uint32_t *prev, uint64_t n_ch
 cudaError_t launch_patch_layout(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
                                 const uint32_t *dlist, uint64_t *patch_rec, uint64_t *patch_data,
                                 uint64_t *dstart, const CallParams *cp, Result *res, cudaStream_t st);
+// Range forms for a checkpoint processed in groups of allocations: diff the
+// chunks [c0, c0 + n) after the `run` entries already listed (gbeg / gcnt
+// get the range's first position and count); lay out and write the records
+// of allocations [a0, a0 + na), continuing the patch offset in run_off.
+cudaError_t launch_diff_range(const uint32_t *cur, const uint32_t *prev, uint64_t c0, uint64_t n,
+                              unsigned int *blockcnt, unsigned long long *blockoff, uint32_t *dlist,
+                              unsigned long long *run, unsigned long long *gbeg, unsigned long long *gcnt,
+                              cudaStream_t st);
+cudaError_t launch_patch_layout_range(const AllocDesc *allocs, uint64_t a0, uint64_t na, uint64_t chunk_bytes,
+                                      const uint32_t *dlist, uint64_t *patch_rec, uint64_t *patch_data,
+                                      uint64_t *dstart, const CallParams *cp, Result *res,
+                                      unsigned long long *run_off, cudaStream_t st);
+cudaError_t launch_patch_meta_range(const AllocDesc *allocs, uint64_t a0, uint64_t na, uint64_t chunk_bytes,
+                                    const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
+                                    const uint64_t *patch_data, const uint64_t *dstart, const Result *res,
+                                    const CallParams *cp, cudaStream_t st);
 cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
                               const uint32_t *cur, const uint32_t *dlist, const uint64_t *patch_rec,
                               const uint64_t *patch_data, const uint64_t *dstart,
