@@ -526,3 +526,41 @@ def test_gpt2_state_pipelined_incremental_parity():
     snap.apply_patch(merged, patch.view(used))
     assert np.array_equal(merged, oracle.write_full(cur, C, generation=1)[1])
     s.close()
+
+
+def test_allocation_past_4_gib_offsets():
+    """One allocation of 4 GiB + 12,345 B (chunk offsets past 2^32 bytes) next
+    to a small one: image hashes and bytes of chunks around the 4 GiB mark and
+    the ragged tail equal the oracle's, and restore brings them back."""
+    C = 65536
+    n_big = (4 << 30) + 12345
+    big = torch.empty(n_big, dtype=torch.uint8, device="cuda")
+    for p in range(0, n_big, 1 << 30):
+        q = min(n_big, p + (1 << 30))
+        workloads.torch_random_bytes(big[p:q], 200 + p // (1 << 30))
+    small = torch.from_numpy(workloads.xorshift_bytes(100003, 9, 0)).cuda()
+    s = make_set([small, big], C)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(img, snap.FULL)
+    nb = (n_big + C - 1) // C
+    picks = [0, 1, (1 << 32) // C - 1, (1 << 32) // C, (1 << 32) // C + 1, nb - 2, nb - 1]
+    from struct import unpack_from
+    rec1 = 64 + 32 + 4 * 2
+    rec1 = (rec1 + 4095) // 4096 * 4096 + 100003
+    rec1 = (rec1 + 4095) // 4096 * 4096  # record of the big allocation
+    b, n, data_off, _ = unpack_from("<QQQQ", img.array, rec1)
+    assert b == n_big and n == nb
+    expect = {}
+    for i in picks:
+        lo, hi = i * C, min((i + 1) * C, n_big)
+        chunk = big[lo:hi].cpu().numpy()
+        expect[i] = chunk
+        assert unpack_from("<I", img.array, rec1 + 32 + 4 * i)[0] == oracle.crc32c(chunk), i
+        assert np.array_equal(img.array[data_off + lo: data_off + hi], chunk), i
+    big.zero_()
+    s.restore(img, used)
+    for i in picks:
+        lo, hi = i * C, min((i + 1) * C, n_big)
+        assert np.array_equal(big[lo:hi].cpu().numpy(), expect[i]), i
+    assert s.verify(img, used) == 0
+    s.close()
