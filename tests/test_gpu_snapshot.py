@@ -564,3 +564,37 @@ def test_allocation_past_4_gib_offsets():
         assert np.array_equal(big[lo:hi].cpu().numpy(), expect[i]), i
     assert s.verify(img, used) == 0
     s.close()
+
+
+def test_many_small_allocations_full_and_incremental():
+    """5,000 allocations of 1 B - 20 KiB (most smaller than a chunk, many not a
+    multiple of 16 B): full image and patch equal the oracle's, and restore
+    into zeroed buffers reproduces every byte."""
+    rng = np.random.default_rng(77)
+    sizes = [int(x) for x in rng.integers(1, 20 * 1024, 5000)]
+    # one arena, allocations at 16-byte aligned offsets (as a caching allocator gives)
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += (n + 15) // 16 * 16
+    arena = torch.empty(o, dtype=torch.uint8, device="cuda")
+    workloads.torch_random_bytes(arena, 78)
+    ts = [arena[a: a + n] for a, n in zip(offs, sizes)]
+    C = 4096
+    s = make_set(ts, C)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    used = s.checkpoint(full, snap.FULL)
+    base = readback(ts)
+    assert np.array_equal(full.view(used), oracle.write_full(base, C, 0)[1])
+    picks = sorted(set(int(k) for k in rng.integers(0, len(sizes), 300)))
+    mutate(ts, C, [(k, 0) for k in picks], seed=79)
+    cur = readback(ts)
+    used_p = s.checkpoint(patch, snap.INCREMENTAL)
+    rc, exp, nd = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in base], 1, 0)
+    assert nd == len(picks) and np.array_equal(patch.view(used_p), exp)
+    arena.zero_()
+    s.restore(full, used)
+    for a, b in zip(readback(ts), base):
+        assert np.array_equal(a, b)
+    s.close()
