@@ -41,3 +41,33 @@ def test_strerror_names_every_status():
     for st in range(0, -12, -1):
         assert snap.strerror(st) != "unknown status"
     assert snap.strerror(-99) == "unknown status"
+
+
+def test_no_gpu_means_a_loud_error_not_a_fallback():
+    """Without a CUDA device every compute entry point fails with a status
+    (the binding raises); nothing falls back to a CPU path."""
+    import ctypes
+
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(snap.SnapError):
+        snap.Set(chunk_bytes=65536)
+    out = ctypes.c_void_p()
+    assert snap.lib().snap_host_alloc(4096, ctypes.byref(out)) != snap.OK
+    v = ctypes.c_double()
+    assert snap.lib().snap_link_ceiling(-1, 0, 1 << 20, 1, ctypes.byref(v)) != snap.OK
+    buf = (ctypes.c_uint32 * 4)()
+    assert snap.lib().snap_hash_chunks(ctypes.cast(buf, ctypes.c_void_p), 16, 4096,
+                                       ctypes.cast(buf, ctypes.c_void_p), None) != snap.OK
+
+
+def test_host_only_calls_work_without_a_gpu():
+    """The host-side entry points (status names, the two-phase protocol)
+    need no device."""
+    assert snap.strerror(snap.EPEER) != "unknown status"
+    seen = []
+    rc = snap.coordinate(lambda ph, st: st, lock=lambda: seen.append("l") or 0,
+                         run=lambda: seen.append("r") or 0, commit=lambda: seen.append("c"))
+    assert rc == snap.OK and seen == ["l", "r", "c"]
