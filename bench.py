@@ -1065,6 +1065,34 @@ def run_async(args, rank, world, local, pg):
                        "async_step_ms": med(A), "caller_cost_ms": max(1e-3, med(A) - med(L))}
         if ctas:
             sx.close()
+    # incremental checkpoints after a 10 % clustered mutation: how long the
+    # caller is held, synchronous call against asynchronous cut
+    nchk = [(n + UNIT - 1) // UNIT for n in sizes]
+    c0s = np.concatenate([[0], np.cumsum(nchk)])
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    s.checkpoint(img, snap.FULL)  # the base
+
+    def mutate(seed):
+        for u in workloads.mutation_units(int(c0s[-1]), args.dirty, seed):
+            k = int(np.searchsorted(c0s, u, side="right") - 1)
+            lo = int(u - c0s[k]) * UNIT
+            ts[k][lo: min(lo + UNIT, sizes[k])].bitwise_not_()
+        torch.cuda.synchronize()
+
+    inc_sync, inc_frozen, inc_total = [], [], []
+    for i in range(max(3, args.warmup) + args.steps):
+        mutate(1000 + 2 * i)
+        s.checkpoint(patch, snap.INCREMENTAL)
+        t_sync = s.stats()["total_ms"]
+        mutate(1001 + 2 * i)
+        s.checkpoint_async(patch, snap.INCREMENTAL)
+        s.checkpoint_wait()
+        st = s.stats()
+        if i >= max(3, args.warmup):
+            inc_sync.append(t_sync)
+            inc_frozen.append(st["frozen_ms"])
+            inc_total.append(st["total_ms"])
+            kern += st["kernel_launches"]
     clk = clocks.stop()
     d = sweep[0] if 0 in sweep else next(iter(sweep.values()))
     over_sync = max(1e-3, med(S) - med(L))
@@ -1078,6 +1106,8 @@ def run_async(args, rank, world, local, pg):
                  {"async": {"default_ctas": 8,
                             "by_ctas": {str(k): v for k, v in sweep.items()},
                             "sync_checkpoint_ms": med(sync_ms), "load_ms": med(L), "sync_step_ms": med(S),
+                            "incremental_10pct": {"sync_call_ms": med(inc_sync), "async_frozen_ms": med(inc_frozen),
+                                                  "async_cut_to_commit_ms": med(inc_total)},
                             "caller_cost_sync_ms": over_sync, "sync_equivalent_gbs": B / (over_sync * 1e-3) / 1e9,
                             "matmul_ms": gemm_ms},
                   "roofline": {"bound": "hbm", "kernel": "k_shadow_copy (the cut)", "achieved": cut_gbs,
