@@ -390,6 +390,18 @@ typedef int (*snap_agree_fn)(void *ctx, int phase, int status);
 SNAP_API int snap_checkpoint_coordinated(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used,
                                          snap_agree_fn agree, void *agree_ctx);
 
+/* snap_restore as one rank of a coordinated restore: lock = validate the
+ * image against the set (header, every record) and quiesce, so that a bad
+ * image or a busy set on any rank stops every rank before any device byte
+ * changes; run = the restore; commit = the image's hashes and generation
+ * become the base; abort (another rank failed in its run) = the previous
+ * base stays.  After a successful run the device holds the image's bytes
+ * either way, and an incremental checkpoint against the previous base is
+ * still exact.  Returns OK only if every rank completed; EPEER if this rank
+ * did and another did not. */
+SNAP_API int snap_restore_coordinated(const void *host_image, uint64_t bytes, snap_set s, snap_agree_fn agree,
+                                      void *agree_ctx);
+
 #ifdef __cplusplus
 }
 #endif

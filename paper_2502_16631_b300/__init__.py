@@ -37,7 +37,8 @@ EXPORTS = (
     "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
-    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated", "snap_link_ceiling",
+    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated", "snap_restore_coordinated",
+    "snap_link_ceiling",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
 
@@ -127,6 +128,7 @@ def _lib():
             "snap_coordinate": [P(CoordOps), vp],
             "snap_link_ceiling": [i32, i32, u64, i32, P(ctypes.c_double)],
             "snap_checkpoint_coordinated": [vp, vp, u64, i32, P(u64), AGREE_FN, vp],
+            "snap_restore_coordinated": [vp, u64, vp, AGREE_FN, vp],
             "snap_server_create": [P(vp), u64, u64, P(Opts)],
             "snap_server_destroy": [vp],
             "snap_server_submit": [vp, vp, i32, vp, u64, P(u64)],
@@ -283,6 +285,12 @@ class Set:
         rc = _lib().snap_checkpoint_coordinated(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
                                                 ctypes.byref(used), cb, None)
         return rc, used.value
+
+    def restore_coordinated(self, image, agree, nbytes: int | None = None) -> int:
+        """One rank of a coordinated restore; returns the status."""
+        cb = _agree_callback(agree)
+        return _lib().snap_restore_coordinated(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+                                               cb, None)
 
     def restore(self, image, nbytes: int | None = None) -> None:
         _check(self.restore_status(image, nbytes), "snap_restore")

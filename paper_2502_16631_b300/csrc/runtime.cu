@@ -929,20 +929,18 @@ int snap_checkpoint_coordinated(snap_set s, void *host_image, uint64_t cap, int 
     return rc;
 }
 
-int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
+}  // extern "C"
+
+namespace snapk {
+
+// The lock of a restore: validate the image against the set (header, every
+// record, the hashes into the stage) and quiesce the caller's stream.
+static int restore_lock(snap_set_s *s, const uint8_t *img, uint64_t bytes, ImageHeader &h, double deadline)
 {
-    const double t0 = now_ms();
-    if (!s || !host_image || ((uintptr_t)host_image & 15u)) return SNAP_EINVAL;
-    BusyGuard g(s);
-    if (!g.ok) return SNAP_EBUSY;
-    cudaSetDevice(s->device);
-    const double deadline = t0 + s->timeout_ms;
     int rc = settle(s, deadline);
     if (rc) return rc;
     rc = build_layout(s);
     if (rc) return rc;
-    const uint8_t *img = static_cast<const uint8_t *>(host_image);
-    ImageHeader h{};
     rc = parse_header(img, bytes, &h);
     if (rc) return rc;
     if (h.flags & SNAP_IMG_FLAG_INCREMENTAL) return SNAP_EFORMAT;  // merge patches first
@@ -950,16 +948,20 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
         return SNAP_EFORMAT;
     rc = walk_records(s, img, bytes, h, s->h_hash_stage);
     if (rc) return rc;
-    uint8_t *dimg = mapped_device_ptr(host_image);
-    rc = quiesce(s, deadline);
-    if (rc) return rc;
-    const double tq = now_ms();
+    return quiesce(s, deadline);
+}
+
+// The restore itself, after restore_lock; commits the image's hashes and
+// generation as the base.
+static int restore_run(snap_set_s *s, const uint8_t *img, uint64_t bytes, const ImageHeader &h, double t0, double tq,
+                       double deadline)
+{
+    uint8_t *dimg = mapped_device_ptr(img);
     if (!dimg) {
         ImageIO io;
         io.mem = const_cast<uint8_t *>(img);  // read only: restore copies image -> ring
         return ring_restore(s, io, h, t0, tq, deadline);
     }
-
     const int cur = 1 - s->prev_idx;
     reset_call(s, dimg, bytes);
     Job j = base_job(s, OP_SCATTER);
@@ -967,7 +969,7 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
     s->h_cb->jobs[0] = j;
     const TileShape sh = s->shape[SHAPE_SCATTER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
-    rc = run_graph(s, GK_RESTORE, cur, [&](cudaStream_t q) {
+    int rc = run_graph(s, GK_RESTORE, cur, [&](cudaStream_t q) {
         cudaError_t e = enqueue_prologue(s, q);
         if (e == cudaSuccess && s->n_chunks)
             e = cudaMemcpyAsync(s->d_hash[cur], s->h_hash_stage, s->n_chunks * 4, cudaMemcpyHostToDevice, q);
@@ -994,6 +996,94 @@ int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
     st.frozen_ms = st.total_ms;
     s->last = st;
     return SNAP_OK;
+}
+
+// One rank of a coordinated restore (snap_coordinate's steps).
+struct CoordRestore {
+    snap_set_s *s;
+    const uint8_t *img;
+    uint64_t bytes;
+    snap_agree_fn agree;
+    void *agree_ctx;
+    bool busy = false;
+    ImageHeader h{};
+    double t0 = 0, tq = 0, deadline = 0;
+    int prev_idx = 0;
+    bool has_base = false;
+    uint64_t base_gen = 0, next_gen = 0;
+};
+
+static int coord_restore_lock(void *p)
+{
+    CoordRestore &c = *static_cast<CoordRestore *>(p);
+    if (!c.s || !c.img || ((uintptr_t)c.img & 15u)) return SNAP_EINVAL;
+    if (c.s->busy.exchange(true)) return SNAP_EBUSY;
+    c.busy = true;
+    cudaSetDevice(c.s->device);
+    c.deadline = c.t0 + c.s->timeout_ms;
+    const int rc = restore_lock(c.s, c.img, c.bytes, c.h, c.deadline);
+    c.tq = now_ms();
+    return rc;
+}
+
+static int coord_restore_run(void *p)
+{
+    CoordRestore &c = *static_cast<CoordRestore *>(p);
+    c.prev_idx = c.s->prev_idx;
+    c.has_base = c.s->has_base;
+    c.base_gen = c.s->base_gen;
+    c.next_gen = c.s->next_gen;
+    return restore_run(c.s, c.img, c.bytes, c.h, c.t0, c.tq, c.deadline);
+}
+
+static void coord_restore_abort(void *p)
+{
+    CoordRestore &c = *static_cast<CoordRestore *>(p);
+    c.s->prev_idx = c.prev_idx;
+    c.s->has_base = c.has_base;
+    c.s->base_gen = c.base_gen;
+    c.s->next_gen = c.next_gen;
+}
+
+static int coord_restore_agree(void *p, int phase, int status)
+{
+    CoordRestore &c = *static_cast<CoordRestore *>(p);
+    return c.agree(c.agree_ctx, phase, status);
+}
+
+}  // namespace snapk
+
+extern "C" {
+
+int snap_restore(const void *host_image, uint64_t bytes, snap_set s)
+{
+    const double t0 = now_ms();
+    if (!s || !host_image || ((uintptr_t)host_image & 15u)) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const double deadline = t0 + s->timeout_ms;
+    const uint8_t *img = static_cast<const uint8_t *>(host_image);
+    ImageHeader h{};
+    const int rc = restore_lock(s, img, bytes, h, deadline);
+    if (rc) return rc;
+    return restore_run(s, img, bytes, h, t0, now_ms(), deadline);
+}
+
+int snap_restore_coordinated(const void *host_image, uint64_t bytes, snap_set s, snap_agree_fn agree,
+                             void *agree_ctx)
+{
+    if (!s || !agree) return SNAP_EINVAL;
+    CoordRestore c{s, static_cast<const uint8_t *>(host_image), bytes, agree, agree_ctx};
+    c.t0 = now_ms();
+    snap_coord_ops ops{};
+    ops.lock = coord_restore_lock;
+    ops.run = coord_restore_run;
+    ops.abort = coord_restore_abort;
+    ops.agree = coord_restore_agree;
+    const int rc = coordinate(ops, &c);
+    if (c.busy) s->busy.store(false);
+    return rc;
 }
 
 int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uint64_t *n_mismatch)

@@ -120,3 +120,42 @@ def test_coordinated_commit_and_peer_failures(pinned):
     rc, _ = s.checkpoint_coordinated(patch, agree, snap.FULL, cap=4096)
     assert rc == snap.EINVAL and agree.calls == [(0, snap.EINVAL)]
     s.close()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_coordinated_restore_validates_everywhere_first(pinned):
+    ts, hs = device_state(SIZES, seed=121)
+    s = make_set(ts)
+    n = sum(oracle.n_chunks(x, C) for x in SIZES)
+    rc, exp = oracle.write_full(hs, C, 7)
+    img = snap.HostBuffer(exp.size) if pinned else np.empty(exp.size, np.uint8)
+    (img.array if pinned else img)[:] = exp
+    s.checkpoint(snap.HostBuffer(s.image_bytes(snap.FULL)), snap.FULL)  # a base at generation 0
+    h0, g0 = s.committed_hashes(n)
+    for t in ts:
+        t.zero_()
+    # a peer whose image is bad: nothing changes here
+    agree = peer_fails_at(0)
+    assert s.restore_coordinated(img, agree) == snap.EPEER and agree.calls == [(0, 0)]
+    assert all(not t.numel() or int(t.max().item()) == 0 for t in ts)
+    # a peer that fails during its run: this rank's bytes are back, its base stays
+    agree = peer_fails_at(1)
+    assert s.restore_coordinated(img, agree) == snap.EPEER and agree.calls == [(0, 0), (1, 0)]
+    for a, b in zip(readback(ts), hs):
+        assert np.array_equal(a, b)
+    h1, g1 = s.committed_hashes(n)
+    assert g1 == g0 and np.array_equal(h1, h0)
+    # everyone succeeds: the image's generation and hashes are the base
+    for t in ts:
+        t.zero_()
+    assert s.restore_coordinated(img, alone) == snap.OK
+    for a, b in zip(readback(ts), hs):
+        assert np.array_equal(a, b)
+    h2, g2 = s.committed_hashes(n)
+    assert g2 == 7 and np.array_equal(h2, np.concatenate([oracle.chunk_hashes(h, C) for h in hs]))
+    # a bad image on this rank is agreed as a failure before anything moves
+    bad = exp.copy()
+    bad[0] ^= 1
+    agree = peer_fails_at(-1)
+    assert s.restore_coordinated(bad, agree) == snap.EFORMAT and agree.calls == [(0, snap.EFORMAT)]
+    s.close()
