@@ -52,7 +52,10 @@ int async_prepare(snap_set_s *s)
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_allocs_shadow, na * sizeof(AllocDesc));
     if (e == cudaSuccess && !s->desc.empty()) {
         std::vector<AllocDesc> sh(s->desc);
-        for (AllocDesc &a : sh) a.ptr = (uint64_t)(uintptr_t)(s->d_shadow + a.state_off);
+        for (AllocDesc &a : sh) {
+            a.ptr = (uint64_t)(uintptr_t)(s->d_shadow + a.state_off);
+            a.tmap = 0;  // the tensor maps describe the registered buffers, not the shadow
+        }
         e = cudaMemcpy(s->d_allocs_shadow, sh.data(), sh.size() * sizeof(AllocDesc), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {

@@ -106,6 +106,13 @@ __device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint3
         "l"(src), "r"(bytes), "r"(mbar)
         : "memory");
 }
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -278,7 +285,8 @@ __device__ __forceinline__ void seg_issue(WarpCtx &w, const uint8_t *src, uint32
 // the same up to a k*P offset, so each lane keeps one source and one
 // destination base; the CRC loop over the piece is fully unrolled.
 template <int P>
-__device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, const CombineConsts &cc, uint32_t &out)
+__device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, const CombineConsts &cc, uint32_t &out,
+                                uint64_t tmap, uint32_t row0)
 {
     constexpr uint32_t BPP = P / 16;    // 16-byte blocks per piece
     constexpr uint32_t PPI = 32 / BPP;  // pieces covered by one warp instruction
@@ -292,16 +300,32 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
     const uint32_t rsw = swz<BPP>(lane);
     uint32_t crc = lane == 0 ? 0xFFFFFFFFu : 0u;
 
+    // stage k: one TMA box (P bytes of each of the 32 segment rows, placed
+    // with the hardware swizzle) when the allocation has a tensor map, else
+    // cp.async copies by every lane into the same swizzled layout
     auto issue = [&](uint32_t k) {
         const uint32_t buf = issue_advance(w);
         const uint32_t sbs = stage0 + buf * w.stage_bytes;
+        const uint32_t mb = w.mbar + 8 * buf;
+        if (tmap) {
+            if (lane == 0) {
+                mbar_arrive_tx(mb, 32u * P);
+                tma_load_2d(sbs, tmap, (int)(k * P), (int)row0, mb);
+            } else {
+                mbar_arrive(mb);
+            }
+            return;
+        }
 #pragma unroll
         for (uint32_t m = 0; m < BPP; ++m) {
             const uint32_t j = jl + m * PPI;
             cp_async16(sbs + j * P + 16u * (bl ^ swz<BPP>(j)), sp0 + m * PPI * s + k * P);
         }
-        cp_async_arrive(w.mbar + 8 * buf);
+        cp_async_arrive(mb);
     };
+    // the stages were last touched through the generic proxy: order that
+    // before the TMA writes into them
+    if (tmap) fence_proxy_async();
     const uint32_t pre = nst < S ? nst : S;
     for (uint32_t k = 0; k < pre; ++k) issue(k);
     for (uint32_t k = 0; k < nst; ++k) {
@@ -312,7 +336,10 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
 #pragma unroll
         for (uint32_t b = 0; b < BPP; ++b) crc = crc_block(crc, lds128(rd + 16u * (b ^ rsw)), w.l4);
         __syncwarp();
-        if (k + S < nst) issue(k + S);
+        if (k + S < nst) {
+            if (tmap) fence_proxy_async();
+            issue(k + S);
+        }
     }
     out = warp_xor(gf2_mulmod(crc, cc.kseg[lane])) ^ 0xFFFFFFFFu;
     return true;
@@ -372,8 +399,10 @@ __device__ bool hash_full_chunk2(WarpCtx &w, const uint8_t *src, uint32_t C, con
 }
 
 // The chunk's CRC-32C lands in `out` in every lane; false if a wait gave up.
+// tmap_base: the allocation's tensor maps (0: none); row0 = 32 x the
+// chunk's index in its allocation (its first segment row).
 __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint32_t C, const CombineConsts &cc,
-                               uint32_t &out)
+                               uint32_t &out, uint64_t tmap_base, uint32_t row0)
 {
     if (w.chains == 2 && L == C && ((C >> 6) % (uint32_t)w.piece) == 0u) {
         switch (w.piece) {
@@ -384,11 +413,12 @@ __device__ bool hash_chunk_seg(WarpCtx &w, const uint8_t *src, uint32_t L, uint3
         }
     }
     if (L == C && ((C >> 5) % (uint32_t)w.piece) == 0u) {
+        const uint64_t tb = tmap_base;
         switch (w.piece) {
-        case 32: return hash_full_chunk<32>(w, src, C, cc, out);
-        case 64: return hash_full_chunk<64>(w, src, C, cc, out);
-        case 128: return hash_full_chunk<128>(w, src, C, cc, out);
-        case 256: return hash_full_chunk<256>(w, src, C, cc, out);
+        case 32: return hash_full_chunk<32>(w, src, C, cc, out, tb ? tb : 0, row0);
+        case 64: return hash_full_chunk<64>(w, src, C, cc, out, tb ? tb + kTmapBytes : 0, row0);
+        case 128: return hash_full_chunk<128>(w, src, C, cc, out, tb ? tb + 2 * kTmapBytes : 0, row0);
+        case 256: return hash_full_chunk<256>(w, src, C, cc, out, 0, row0);
         default: break;
         }
     }
@@ -676,7 +706,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
         switch (jb.op) {
         case OP_HASH:
         case OP_VERIFY:
-            ok = hash_chunk_seg(w, dsrc, L, (uint32_t)C, cc, h);
+            ok = hash_chunk_seg(w, dsrc, L, (uint32_t)C, cc, h, ad.tmap, (uint32_t)(i * 32u));
             if (ok && lane == 0) {
                 if (jb.hash_out) jb.hash_out[chunk] = h;
                 if (jb.op == OP_VERIFY && jb.hash_cmp[chunk] != h) {

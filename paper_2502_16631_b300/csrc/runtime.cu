@@ -9,6 +9,8 @@
 #include "crc32c_gf2.h"
 #include "runtime_internal.h"
 
+#include <cuda.h>  // CUtensorMap and its encoding parameters (the encoder comes through the runtime)
+
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
@@ -173,6 +175,8 @@ static void free_device(snap_set_s *s)
     for (auto &g : s->graphs) if (g.exec) cudaGraphExecDestroy(g.exec);
     s->graphs.clear();
     cudaFree(s->d_allocs);
+    cudaFree(s->d_tmaps);
+    s->d_tmaps = nullptr;
     cudaFree(s->d_hash[0]);
     cudaFree(s->d_hash[1]);
     cudaFree(s->d_cmp);
@@ -220,6 +224,72 @@ static void plan_groups(snap_set_s *s)
     s->gch[s->n_groups] = s->n_chunks;
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor maps for the hash staging: allocation k viewed as rows of C/32
+// bytes (floor(bytes / (C/32)) rows, so only whole rows: every full chunk
+// is covered, ragged chunks take the cp.async path), one map per piece size
+// 32 / 64 / 128 with the matching 32 / 64 / 128-byte swizzle.  Allocations
+// without a full chunk, or whose maps cannot be encoded, keep tmap = 0.
+static int build_tensor_maps(snap_set_s *s)
+{
+    const EncodeTiledFn enc = encode_tiled();
+    const size_t n = s->desc.size();
+    if (!enc || n == 0) return SNAP_OK;
+    const uint64_t row = s->C / 32;
+    std::vector<CUtensorMap> maps(n * kTmapPieces);
+    std::vector<char> ok(n, 0);
+    for (size_t k = 0; k < n; ++k) {
+        const AllocDesc &a = s->desc[k];
+        if (a.bytes < s->C) continue;
+        bool good = true;
+        for (int pi = 0; pi < kTmapPieces && good; ++pi) {
+            const cuuint32_t piece = 32u << pi;
+            const cuuint64_t dim[2] = {row, a.bytes / row};
+            const cuuint64_t stride[1] = {row};
+            const cuuint32_t box[2] = {piece, 32};
+            const cuuint32_t estride[2] = {1, 1};
+            const CUtensorMapSwizzle sw = pi == 0 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                        : pi == 1 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                  : CU_TENSOR_MAP_SWIZZLE_128B;
+            good = enc(&maps[k * kTmapPieces + pi], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                       reinterpret_cast<void *>(a.ptr), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        }
+        ok[k] = good;
+    }
+    static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+    cudaError_t e = cudaMalloc((void **)&s->d_tmaps, maps.size() * sizeof(CUtensorMap));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(s->d_tmaps);
+        s->d_tmaps = nullptr;
+        return cuda_status(e);
+    }
+    for (size_t k = 0; k < n; ++k)
+        s->desc[k].tmap = ok[k] ? (uint64_t)(uintptr_t)(s->d_tmaps + k * kTmapPieces * kTmapBytes) : 0;
+    return SNAP_OK;
+}
+
 int build_layout(snap_set_s *s)
 {
     if (!s->layout_dirty) return SNAP_OK;
@@ -232,6 +302,7 @@ int build_layout(snap_set_s *s)
         AllocDesc &a = s->desc[k];
         a.ptr = (uint64_t)(uintptr_t)s->allocs[k].ptr;
         a.bytes = s->allocs[k].bytes;
+        a.tmap = 0;  // set by build_tensor_maps
         const uint64_t nk = (a.bytes + C - 1) / C;
         a.chunk0 = chunk;
         a.rec_off = off;
@@ -270,6 +341,13 @@ int build_layout(snap_set_s *s)
     al((void **)&s->d_patch_data, na * 8);
     al((void **)&s->d_dstart, (na + 1) * 8);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_hash_stage, nc * 4, cudaHostAllocDefault);
+    if (e == cudaSuccess) {
+        const int rc = build_tensor_maps(s);
+        if (rc) {
+            free_device(s);
+            return rc;
+        }
+    }
     if (e == cudaSuccess && !s->desc.empty())
         e = cudaMemcpy(s->d_allocs, s->desc.data(), s->desc.size() * sizeof(AllocDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -70,6 +70,7 @@ struct snap_set_s {
 
     // device arrays (rebuilt with the layout)
     snapk::AllocDesc *d_allocs = nullptr;
+    uint8_t *d_tmaps = nullptr;  // kTmapPieces tensor maps per allocation (hash staging)
     uint32_t *d_hash[2] = {nullptr, nullptr};  // committed table = d_hash[prev_idx]
     uint32_t *d_cmp = nullptr;                 // verify: expected hashes
     unsigned int *d_blockcnt = nullptr;

@@ -16,7 +16,17 @@ struct AllocDesc {
     uint64_t data_off;   // full image: offset of its data (4 KiB aligned)
     uint64_t state_off;  // offset in the packed concatenation of all allocations
                          // (each allocation starts on a 256-byte boundary)
+    uint64_t tmap;       // device address of its three TMA tensor maps (pieces of
+                         // 32, 64, 128 bytes; kTmapBytes each) for the hash
+                         // staging, or 0: stage with cp.async instead
 };
+
+// A 2D view of an allocation for the hash staging: rows of C/32 bytes (one
+// lane segment each), box = piece bytes x 32 rows, so stage k of full chunk
+// i is the box at (k * piece, 32 * i).  The box lands in shared memory with
+// the hardware swizzle that equals the stage layout's XOR swizzle.
+constexpr uint32_t kTmapBytes = 128;
+constexpr int kTmapPieces = 3;  // 32, 64, 128
 
 // What a job does with each of its chunk tiles.
 enum JobOp : uint32_t {
