@@ -321,6 +321,9 @@ typedef struct {
     uint32_t piece_bytes;  /* bytes each lane stages per step        */
     uint32_t ctas_per_sm;
     double gbs;            /* measured throughput of the winner      */
+    uint32_t chains;       /* hashing: CRC chains per lane (1 or 2)  */
+    uint32_t tma;          /* hashing: 1 = stages loaded by 2D TMA tensor
+                              copies, 0 = by per-lane cp.async       */
 } snap_tuning;
 
 /* Time the set's hash pass (mode SNAP_INCREMENTAL) or full gather (SNAP_FULL)

@@ -83,7 +83,7 @@ class CoordOps(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_uint32), ("stages", ctypes.c_uint32),
                 ("piece_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("gbs", ctypes.c_double)]
+                ("gbs", ctypes.c_double), ("chains", ctypes.c_uint32), ("tma", ctypes.c_uint32)]
 
 
 _LIB = None

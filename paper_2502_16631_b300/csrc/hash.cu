@@ -12,6 +12,7 @@ namespace snapk {
 namespace {
 
 struct HashScratch {
+    alignas(128) uint8_t maps[kTmapPieces * kTmapBytes];  // the buffer's tensor maps (hash staging)
     AllocDesc desc;
     unsigned long long cursor;
     unsigned long long pad;
@@ -79,6 +80,7 @@ extern "C" int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk
     std::memset(&h, 0, sizeof h);
     h.desc.ptr = (uint64_t)(uintptr_t)dptr;
     h.desc.bytes = bytes;
+    if (encode_hash_maps(h.desc.ptr, bytes, chunk_bytes, h.maps)) h.desc.tmap = (uint64_t)(uintptr_t)c.d->maps;
     h.res.first_bad = ~0ull;
     h.job.allocs = &c.d->desc;
     h.job.n_allocs = 1;

@@ -113,6 +113,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, uint64_t tmap, int x, 
         ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(mbar)
         : "memory");
 }
+// The tensor maps live in global memory and are rewritten between launches
+// (the standalone hasher reuses one slot): make the tensor-map proxy see the
+// latest contents before using one.
+__device__ __forceinline__ void tmap_acquire(uint64_t tmap)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
@@ -210,6 +217,8 @@ struct WarpCtx {
     int stages, piece, lane, chains;
     uint32_t lb;           // shared address of this lane's table column
     uint32_t l4;           // lane * 4 (the column offset inside a table row)
+    bool tma;              // stage full chunks with TMA tensor copies where possible
+    uint64_t tmap_seen;    // the tensor map this warp last acquired
     uint32_t stage_bytes;  // 32 * chains * piece
 };
 
@@ -325,7 +334,13 @@ __device__ bool hash_full_chunk(WarpCtx &w, const uint8_t *src, uint32_t C, cons
     };
     // the stages were last touched through the generic proxy: order that
     // before the TMA writes into them
-    if (tmap) fence_proxy_async();
+    if (tmap) {
+        fence_proxy_async();
+        if (tmap != w.tmap_seen) {  // once per map per warp and launch
+            if (lane == 0) tmap_acquire(tmap);
+            w.tmap_seen = tmap;
+        }
+    }
     const uint32_t pre = nst < S ? nst : S;
     for (uint32_t k = 0; k < pre; ++k) issue(k);
     for (uint32_t k = 0; k < nst; ++k) {
@@ -592,7 +607,8 @@ __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, u
 template <bool HASH_ONLY>
 __global__ void __launch_bounds__(HASH_ONLY ? kMaxHashWarps * 32 : kMaxWarps * 32, 1)
 snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long long *cursor,
-           unsigned long long *cursor_b, const CombineConsts cc, int stages, int piece, int chains, Result *kres)
+           unsigned long long *cursor_b, const CombineConsts cc, int stages, int piece, int chains, int tma,
+           Result *kres)
 {
     // Jobs [0, n_jobs_a) form group A (device -> host work), jobs
     // [n_jobs_a, n_jobs) group B (host -> device work); each group has its own
@@ -650,6 +666,8 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
     w.stages = stages;
     w.piece = piece;
     w.chains = chains;
+    w.tma = tma != 0;
+    w.tmap_seen = 0;
     w.lane = lane;
     w.lb = smem_addr(tables) + 4u * (uint32_t)lane;
     w.l4 = 4u * (uint32_t)lane;
@@ -706,7 +724,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
         switch (jb.op) {
         case OP_HASH:
         case OP_VERIFY:
-            ok = hash_chunk_seg(w, dsrc, L, (uint32_t)C, cc, h, ad.tmap, (uint32_t)(i * 32u));
+            ok = hash_chunk_seg(w, dsrc, L, (uint32_t)C, cc, h, w.tma ? ad.tmap : 0ull, (uint32_t)(i * 32u));
             if (ok && lane == 0) {
                 if (jb.hash_out) jb.hash_out[chunk] = h;
                 if (jb.op == OP_VERIFY && jb.hash_cmp[chunk] != h) {
@@ -783,10 +801,10 @@ cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigne
         return cudaErrorInvalidValue;
     if (sh.warps > kMaxWarps)
         snap_tiles<true><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
-                                                               sh.stages, sh.piece, sh.chains, kres);
+                                                               sh.stages, sh.piece, sh.chains, sh.tma, kres);
     else
         snap_tiles<false><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
-                                                                sh.stages, sh.piece, sh.chains, kres);
+                                                                sh.stages, sh.piece, sh.chains, sh.tma, kres);
     return cudaGetLastError();
 }
 

@@ -245,39 +245,46 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// Tensor maps for the hash staging: allocation k viewed as rows of C/32
-// bytes (floor(bytes / (C/32)) rows, so only whole rows: every full chunk
-// is covered, ragged chunks take the cp.async path), one map per piece size
-// 32 / 64 / 128 with the matching 32 / 64 / 128-byte swizzle.  Allocations
-// without a full chunk, or whose maps cannot be encoded, keep tmap = 0.
+// The hash staging's tensor maps of one buffer: viewed as rows of C/32 bytes
+// (floor(bytes / (C/32)) rows, so only whole rows: every full chunk is
+// covered, ragged chunks take the cp.async path), one map per piece size
+// 32 / 64 / 128 with the matching 32 / 64 / 128-byte swizzle, into `out`
+// (kTmapPieces x kTmapBytes).  False if the buffer has no full chunk or a
+// map cannot be encoded.
+bool encode_hash_maps(uint64_t ptr, uint64_t bytes, uint64_t C, void *out)
+{
+    static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc || bytes < C || (ptr & 15u)) return false;
+    const uint64_t row = C / 32;
+    CUtensorMap *maps = static_cast<CUtensorMap *>(out);
+    for (int pi = 0; pi < kTmapPieces; ++pi) {
+        const cuuint32_t piece = 32u << pi;
+        const cuuint64_t dim[2] = {row, bytes / row};
+        const cuuint64_t stride[1] = {row};
+        const cuuint32_t box[2] = {piece, 32};
+        const cuuint32_t estride[2] = {1, 1};
+        const CUtensorMapSwizzle sw = pi == 0 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                    : pi == 1 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                              : CU_TENSOR_MAP_SWIZZLE_128B;
+        if (enc(&maps[pi], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, reinterpret_cast<void *>(ptr), dim, stride, box,
+                estride, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+// Tensor maps for every allocation of the set (allocations without a full
+// chunk, or whose maps cannot be encoded, keep tmap = 0).
 static int build_tensor_maps(snap_set_s *s)
 {
-    const EncodeTiledFn enc = encode_tiled();
     const size_t n = s->desc.size();
-    if (!enc || n == 0) return SNAP_OK;
-    const uint64_t row = s->C / 32;
+    if (!encode_tiled() || n == 0) return SNAP_OK;
     std::vector<CUtensorMap> maps(n * kTmapPieces);
     std::vector<char> ok(n, 0);
-    for (size_t k = 0; k < n; ++k) {
-        const AllocDesc &a = s->desc[k];
-        if (a.bytes < s->C) continue;
-        bool good = true;
-        for (int pi = 0; pi < kTmapPieces && good; ++pi) {
-            const cuuint32_t piece = 32u << pi;
-            const cuuint64_t dim[2] = {row, a.bytes / row};
-            const cuuint64_t stride[1] = {row};
-            const cuuint32_t box[2] = {piece, 32};
-            const cuuint32_t estride[2] = {1, 1};
-            const CUtensorMapSwizzle sw = pi == 0 ? CU_TENSOR_MAP_SWIZZLE_32B
-                                        : pi == 1 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                                  : CU_TENSOR_MAP_SWIZZLE_128B;
-            good = enc(&maps[k * kTmapPieces + pi], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
-                       reinterpret_cast<void *>(a.ptr), dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-        }
-        ok[k] = good;
-    }
-    static_assert(sizeof(CUtensorMap) == kTmapBytes, "tensor map size");
+    for (size_t k = 0; k < n; ++k)
+        ok[k] = encode_hash_maps(s->desc[k].ptr, s->desc[k].bytes, s->C, &maps[k * kTmapPieces]);
     cudaError_t e = cudaMalloc((void **)&s->d_tmaps, maps.size() * sizeof(CUtensorMap));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

@@ -202,6 +202,10 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
                      GraphEntry **out);
 int complete_checkpoint(snap_set_s *s, int mode, int cur, uint8_t *host_image, uint64_t *used, snap_stats &st);
 
+// Tensor maps of one buffer for the hash staging (runtime.cu): writes
+// kTmapPieces x kTmapBytes to `out`; false if the buffer cannot use them.
+bool encode_hash_maps(uint64_t ptr, uint64_t bytes, uint64_t chunk_bytes, void *out);
+
 // two-phase coordination across ranks (coord.cu)
 int coordinate(const snap_coord_ops &o, void *ctx);
 

@@ -96,6 +96,10 @@ struct TileShape {
     int piece;        // bytes per segment per stage: 32, 64, 128 or 256
     int ctas;         // grid size (persistent CTAs)
     int chains = 1;   // hashing: independent CRC chains per lane (1 or 2)
+    int tma = 0;      // hashing: 1 = stage full chunks with 2D TMA tensor copies where
+                      // the allocation has tensor maps, 0 = per-lane cp.async (the
+                      // autotuner picks per set: within 3 % of each other at the
+                      // best shapes, TMA ahead at large chunks)
 };
 
 // Combine constants, computed on the host for a chunk size and piece size.

@@ -68,9 +68,9 @@ static void cache_store(const snap_set_s *s, int mode, const TileShape &t, doubl
     FILE *f = std::fopen(p.c_str(), "a");
     if (!f) return;
     std::fprintf(f, "{\"gpu\": \"%s\", \"op\": %d, \"chunk\": %llu, \"class\": %d, \"warps\": %d, \"stages\": %d, "
-                    "\"piece\": %d, \"ctas\": %d, \"gbs\": %.3f}\n",
+                    "\"piece\": %d, \"chains\": %d, \"tma\": %d, \"ctas\": %d, \"gbs\": %.3f}\n",
                  s->gpu_name, mode, (unsigned long long)s->C, size_class(s->total_bytes), t.warps, t.stages, t.piece,
-                 t.ctas, gbs);
+                 t.chains, t.tma, t.ctas, gbs);
     std::fclose(f);
 }
 
@@ -148,8 +148,10 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
     for (int a = 0; a < nwl; ++a)
         for (int b = 0; b < 3; ++b)
             for (int c = 0; c < np; ++c)
-                for (int h = 1; h <= nch; ++h) {
-                TileShape t{wl[a], stages_c[b], pl[c], s->sms * cps, h};
+                for (int h = 1; h <= nch; ++h)
+                for (int tm = 0; tm <= (mode == SNAP_FULL || h == 2 || pl[c] > 128 ? 0 : 1); ++tm) {
+                // TMA staging exists for one chain per lane and pieces up to 128 bytes
+                TileShape t{wl[a], stages_c[b], pl[c], s->sms * cps, h, mode == SNAP_FULL ? 1 : tm};
                 if (tile_smem_bytes(t) > kMaxSmem) continue;
                 double ms = 0, m2 = 0;
                 rc = time_shape(s, op, dimg, t, &ms);  // warm
@@ -165,9 +167,9 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
                 else if (cur != ref) return SNAP_ECUDA;
                 if (std::getenv("SNAP_TUNE_LOG"))
                     std::fprintf(stderr,
-                                 "snap_autotune op=%d warps=%d stages=%d piece=%d chains=%d ctas=%d: %.3f ms, "
+                                 "snap_autotune op=%d warps=%d stages=%d piece=%d chains=%d tma=%d ctas=%d: %.3f ms, "
                                  "%.1f GB/s\n",
-                                 mode, t.warps, t.stages, t.piece, t.chains, t.ctas, ms,
+                                 mode, t.warps, t.stages, t.piece, t.chains, t.tma, t.ctas, ms,
                                  (double)s->total_bytes / (ms * 1e-3) / 1e9);
                 if (ms < best_ms) {
                     best_ms = ms;
@@ -186,6 +188,8 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
         out->piece_bytes = (uint32_t)best.piece;
         out->ctas_per_sm = (uint32_t)cps;
         out->gbs = gbs;
+        out->chains = (uint32_t)best.chains;
+        out->tma = (uint32_t)best.tma;
     }
     return SNAP_OK;
 }
