@@ -86,6 +86,9 @@ typedef struct {
     uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB */
     uint32_t async_ctas;   /* CTAs of the background part of snap_checkpoint_async;
                               default 8 (enough to saturate the host link) */
+    uint32_t hash_tma;     /* 1: stage the hash pass with 2D TMA tensor copies
+                              (else per-lane cp.async; snap_autotune may
+                              change it) */
 } snap_opts;
 
 /* Per-call statistics (times in milliseconds; quiesce_ms and total_ms are

@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint64), ("timeout_ms", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("ctas_per_sm", ctypes.c_uint32), ("stages", ctypes.c_uint32),
-                ("ring_bytes", ctypes.c_uint64), ("async_ctas", ctypes.c_uint32)]
+                ("ring_bytes", ctypes.c_uint64), ("async_ctas", ctypes.c_uint32), ("hash_tma", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -209,9 +209,10 @@ class Set:
     """A set of registered device allocations (snap_set)."""
 
     def __init__(self, chunk_bytes: int = 0, timeout_ms: int = 0, device: int = -1, stream=None,
-                 ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0, async_ctas: int = 0):
+                 ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0, async_ctas: int = 0,
+                 hash_tma: bool = False):
         o = Opts(chunk_bytes, timeout_ms, device, _stream_handle(stream), ctas_per_sm, stages, ring_bytes,
-                 async_ctas)
+                 async_ctas, 1 if hash_tma else 0)
         h = ctypes.c_void_p()
         _check(_lib().snap_set_create(ctypes.byref(h), ctypes.byref(o)), "snap_set_create")
         self.h = h.value

@@ -36,6 +36,7 @@ void default_shapes(snap_set_s *s)
     const int c = s->sms * ctas_per_sm(s);
     s->shape[SHAPE_GATHER] = TileShape{4, 2, 256, c, 1};
     s->shape[SHAPE_HASH] = default_hash_shape(c);
+    s->shape[SHAPE_HASH].tma = s->opts.hash_tma ? 1 : 0;
     s->shape[SHAPE_SCATTER] = TileShape{16, 1, 64, c, 1};
     if (s->opts.stages)
         for (int k = 0; k < SHAPE_COUNT; ++k) {

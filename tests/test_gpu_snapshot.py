@@ -598,3 +598,26 @@ def test_many_small_allocations_full_and_incremental():
     for a, b in zip(readback(ts), base):
         assert np.array_equal(a, b)
     s.close()
+
+
+@pytest.mark.parametrize("C", [4096, 65536, 1 << 20])
+def test_tma_hash_staging_parity(C):
+    """The hash pass staged by 2D TMA tensor copies (tensor map per
+    allocation, hardware swizzle) gives the oracle's hashes: full image,
+    incremental patch and verify, with ragged allocations beside full ones."""
+    sizes = SIZES_EDGE + [5 * C + 12345, 3 * C]
+    ts, hs = device_state(sizes, seed=131)
+    s = make_set(ts, C, hash_tma=True)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    used = s.checkpoint(full, snap.FULL)
+    assert np.array_equal(full.view(used), oracle.write_full(hs, C, 0)[1])
+    nch = [(x + C - 1) // C for x in sizes]
+    dirty = [(k, n - 1) for k, n in enumerate(nch) if n] + [(len(sizes) - 2, 2)]
+    mutate(ts, C, dirty, seed=132)
+    cur = readback(ts)
+    used_p = s.checkpoint(patch, snap.INCREMENTAL)
+    rc, exp, nd = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in hs], 1, 0)
+    assert nd == len(set(dirty)) and np.array_equal(patch.view(used_p), exp)
+    assert s.verify(patch, used_p) == 0
+    s.close()
