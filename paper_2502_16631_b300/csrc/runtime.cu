@@ -198,11 +198,13 @@ static void free_device(snap_set_s *s)
 }
 
 // Groups of whole allocations, in registration order, of about equal bytes
-// and at least 64 MiB each, for the pipelined incremental checkpoint (one
-// group: no pipeline).
+// for the pipelined incremental checkpoint (one group: no pipeline).  A
+// group holds at least 64 MiB and 4,096 chunks: each group's dirty chunks
+// are gathered by a few warps, one chunk per warp at a time, so a group
+// with only a handful of dirty (large) chunks would leave the link idle.
 static void plan_groups(snap_set_s *s)
 {
-    const uint64_t kGroupBytes = 64ull << 20;
+    const uint64_t kGroupBytes = std::max<uint64_t>(64ull << 20, 4096 * s->C);
     const size_t n = s->desc.size();
     const int G = (int)std::min<uint64_t>((uint64_t)kMaxGroups, s->total_bytes / kGroupBytes);
     int g = 0;

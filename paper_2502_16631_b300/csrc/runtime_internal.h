@@ -21,7 +21,7 @@ struct ImageHeader {
 
 // A pipelined incremental checkpoint splits the allocations into at most
 // this many groups (whole allocations, in registration order).
-constexpr int kMaxGroups = 8;
+constexpr int kMaxGroups = 16;
 // CTAs that gather dirty chunks while the other SMs hash the next group: the
 // device-to-host link saturates with 8 gather CTAs on B300.
 constexpr int kPipeGatherCtas = 8;

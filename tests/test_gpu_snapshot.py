@@ -438,10 +438,11 @@ def test_link_ceiling_measures_both_directions():
 
 
 def _pipeline_state(seed):
-    """About 330 MiB in 41 allocations of uneven sizes (zero bytes, a few
-    bytes, ragged, one of 100 MiB): five groups of the pipelined incremental."""
+    """About 630 MiB in 41 allocations of uneven sizes (zero bytes, a few
+    bytes, ragged, one of 200 MiB): two groups of the pipelined incremental at
+    64 KiB chunks, nine at 16 KiB."""
     rng = np.random.default_rng(seed)
-    sizes = [int(x) for x in rng.integers(1, 12 * MiB, 36)] + [0, 17, 100 * MiB + 12345, 65536, 3]
+    sizes = [int(x) for x in rng.integers(1, 24 * MiB, 36)] + [0, 17, 200 * MiB + 12345, 65536, 3]
     rng.shuffle(sizes)
     ts = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
     for k, t in enumerate(ts):
