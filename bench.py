@@ -375,7 +375,7 @@ def run_snap(args, rank, world, local, pg):
     grid = arena.view(-1, UNIT)
 
     per = {"full": [], "incr": [], "verify": [], "restore": [], "gather_kernel": [], "scatter_kernel": [],
-           "hash_kernel": [], "diff": [], "dirty_gather": []}
+           "hash_kernel": [], "diff": [], "dirty_gather": [], "verify_kernel": []}
     counts = {"kernels": 0, "patch_bytes": 0, "dirty": 0}
 
     def step(record):
@@ -406,6 +406,7 @@ def run_snap(args, rank, world, local, pg):
             per["gather_kernel"].append(st_full["copy_ms"])
             per["scatter_kernel"].append(st_res["copy_ms"])
             per["hash_kernel"].append(st_incr["hash_ms"])
+            per["verify_kernel"].append(st_ver["hash_ms"])
             per["diff"].append(st_incr["diff_ms"])
             per["dirty_gather"].append(st_incr["copy_ms"])
             counts["kernels"] += sum(int(x["kernel_launches"]) for x in (st_full, st_incr, st_ver, st_res))
@@ -454,7 +455,10 @@ def run_snap(args, rank, world, local, pg):
     achieved = B / (gather_ms * 1e-3) / 1e9
     pk = measured_peaks()
     hbm_peak = pk.get("hbm_gbs", 6400.0)
-    hash_ms = statistics.mean(per["hash_kernel"])
+    # the hash pass alone: the verify call's kernel (hash + compare with the
+    # patch's hashes) over the whole state; the incremental call's hash phase
+    # overlaps its dirty gather (pipelined), so it is not a clean figure
+    hash_ms = statistics.mean(per["verify_kernel"])
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -471,7 +475,7 @@ def run_snap(args, rank, world, local, pg):
                              "sm_path_peak": peaks["sm_h2d"],
                              "frac_of_sm_path": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9
                              / peaks["sm_h2d"]},
-        "roofline_hash": {"bound": "hbm", "kernel": "snap_tiles (OP_HASH, incremental hash pass)",
+        "roofline_hash": {"bound": "hbm", "kernel": "snap_tiles (OP_VERIFY: the hash pass plus the compare)",
                           "achieved": B / (hash_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                           "frac": B / (hash_ms * 1e-3) / 1e9 / hbm_peak,
                           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
@@ -484,7 +488,8 @@ def run_snap(args, rank, world, local, pg):
             "plain_restore_gbs": B / min(plain_r) / 1e9,
             "incremental_vs_plain_full": incr_gbs / plain_ckpt_gbs,
             "dirty_chunks": counts["dirty"], "patch_bytes": counts["patch_bytes"],
-            "hash_ms": hash_ms, "diff_ms": statistics.mean(per["diff"]),
+            "hash_ms": hash_ms, "incremental_hash_phase_ms": statistics.mean(per["hash_kernel"]),
+            "diff_ms": statistics.mean(per["diff"]),
             "dirty_gather_ms": statistics.mean(per["dirty_gather"]),
             "gather_kernel_ms": gather_ms, "scatter_kernel_ms": statistics.mean(per["scatter_kernel"]),
             # per call over the timed steps: median and standard deviation (ms)
