@@ -536,14 +536,15 @@ int async_ctas(const snap_set_s *s)
 static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEntry **out)
 {
     const int G = s->n_groups;
-    if (!s->st_pipe) {
-        const cudaError_t e = cudaStreamCreateWithFlags(&s->st_pipe, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            s->st_pipe = nullptr;
-            return cuda_status(e);
+    for (cudaStream_t *p : {&s->st_pipe, &s->st_meta})
+        if (!*p) {
+            const cudaError_t e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                *p = nullptr;
+                return cuda_status(e);
+            }
         }
-    }
-    for (int i = 0; i < G + 2; ++i)
+    for (int i = 0; i < 2 * G + 1; ++i)
         if (!s->ev_pipe[i]) {
             const cudaError_t e = cudaEventCreateWithFlags(&s->ev_pipe[i], cudaEventDisableTiming);
             if (e != cudaSuccess) return cuda_status(e);
@@ -579,6 +580,12 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEnt
         if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[0], q);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h, s->ev_pipe[0], 0);
         if (e == cudaSuccess) e = launch_stamp(&d->res, TS_DIFF_END, q);  // copy_ms spans the whole pipeline
+        // three streams: h hashes the groups back to back; m takes each
+        // hashed group through diff, layout and metadata (they continue the
+        // running dirty count and patch offset, so they stay in group
+        // order); q gathers each group as soon as its metadata is written
+        cudaStream_t m = s->st_meta;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m, s->ev_pipe[0], 0);
         for (int g = 0; g < G && e == cudaSuccess; ++g) {
             if (s->gch[g + 1] > s->gch[g])
                 e = launch_tiles(d->jobs + g, 1, &d->cursor[g], cch, shh, &d->res, h);
@@ -587,19 +594,26 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEnt
         }
         for (int g = 0; g < G && e == cudaSuccess; ++g) {
             const uint64_t a0 = s->gal[g], na = s->gal[g + 1] - s->gal[g];
-            e = cudaStreamWaitEvent(q, s->ev_pipe[1 + g], 0);
+            e = cudaStreamWaitEvent(m, s->ev_pipe[1 + g], 0);
             if (e == cudaSuccess)
                 e = launch_diff_range(curp, prevp, s->gch[g], s->gch[g + 1] - s->gch[g], s->d_blockcnt,
-                                      s->d_blockoff, s->d_dlist, &d->res.n_dirty, &d->gbeg[g], &d->gcnt[g], q);
+                                      s->d_blockoff, s->d_dlist, &d->res.n_dirty, &d->gbeg[g], &d->gcnt[g], m);
             if (e == cudaSuccess)
                 e = launch_patch_layout_range(s->d_allocs, a0, na, s->C, s->d_dlist, s->d_patch_rec,
-                                              s->d_patch_data, s->d_dstart, &d->cp, &d->res, &d->run_off, q);
+                                              s->d_patch_data, s->d_dstart, &d->cp, &d->res, &d->run_off, m);
             if (e == cudaSuccess)
                 e = launch_patch_meta_range(s->d_allocs, a0, na, s->C, curp, s->d_dlist, s->d_patch_rec,
-                                            s->d_patch_data, s->d_dstart, &d->res, &d->cp, q);
+                                            s->d_patch_data, s->d_dstart, &d->res, &d->cp, m);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[1 + G + g], m);
+        }
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            e = cudaStreamWaitEvent(q, s->ev_pipe[1 + G + g], 0);
             if (e == cudaSuccess)
                 e = launch_tiles(d->jobs + G + g, 1, &d->cursor[G + g], ccg, shg, &d->res, q);
         }
+        // join the hash stream too (its last event precedes the last metadata,
+        // but a join must name the stream's own last work)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q, s->ev_pipe[G], 0);
         if (e == cudaSuccess) e = enqueue_epilogue(s, q);
         return e;
     }, out);
@@ -804,6 +818,7 @@ int snap_set_destroy(snap_set s)
     for (auto &ev : s->ev_pipe)
         if (ev) cudaEventDestroy(ev);
     if (s->st_pipe) cudaStreamDestroy(s->st_pipe);
+    if (s->st_meta) cudaStreamDestroy(s->st_meta);
     cudaFree(s->d_cb);
     cudaFreeHost(s->h_cb);
     cudaFreeHost(s->h_res);

@@ -94,8 +94,8 @@ struct snap_set_s {
     // chunks [gch[g], gch[g+1]); a second stream and its fork/join events
     int n_groups = 0;
     uint64_t gal[snapk::kMaxGroups + 1] = {}, gch[snapk::kMaxGroups + 1] = {};
-    cudaStream_t st_pipe = nullptr;
-    cudaEvent_t ev_pipe[snapk::kMaxGroups + 2] = {};
+    cudaStream_t st_pipe = nullptr, st_meta = nullptr;
+    cudaEvent_t ev_pipe[2 * snapk::kMaxGroups + 1] = {};
 
     std::vector<snapk::GraphEntry> graphs;
     snapk::TileShape shape[snapk::SHAPE_COUNT];
