@@ -205,3 +205,58 @@ def test_async_gpt2_state_full_parity():
     assert rc == 0 and used == exp.size
     assert np.array_equal(img.view(used), exp)
     s.close()
+
+
+def test_two_sets_in_two_threads_and_one_set_shared():
+    """Sets are independent: two threads checkpoint two sets at once and both
+    images equal the oracle's; on one set, a second concurrent call gets
+    SNAP_EBUSY instead of interleaving with the first."""
+    import threading
+    ts1, hs1 = device_state(SIZES, seed=141)
+    ts2, hs2 = device_state(SIZES, seed=142)
+    s1, s2 = make_set(ts1, 65536), make_set(ts2, 65536)
+    i1 = snap.HostBuffer(s1.image_bytes(snap.FULL))
+    i2 = snap.HostBuffer(s2.image_bytes(snap.FULL))
+    out = {}
+
+    def run(name, s, img):
+        out[name] = [s.checkpoint(img, snap.FULL) for _ in range(5)][-1]
+
+    th = [threading.Thread(target=run, args=("a", s1, i1)), threading.Thread(target=run, args=("b", s2, i2))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert np.array_equal(i1.view(out["a"]), oracle.write_full(hs1, 65536, 4)[1])
+    assert np.array_equal(i2.view(out["b"]), oracle.write_full(hs2, 65536, 4)[1])
+    # one set: while an asynchronous checkpoint is pending every call is busy
+    s1.checkpoint_async(i1, snap.FULL)
+    statuses = []
+    th = [threading.Thread(target=lambda: statuses.append(s1.checkpoint_status(i1, snap.FULL)[0]))
+          for _ in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert statuses == [snap.EBUSY] * 4
+    s1.checkpoint_wait()
+    s1.close()
+    s2.close()
+
+
+def test_destroy_with_pending_work_waits_for_it():
+    """Closing a set with an asynchronous checkpoint or a prioritised restore
+    still in flight waits for the device work before freeing anything."""
+    ts, hs = device_state([64 * MiB, 3 * MiB + 5], seed=151)
+    s = make_set(ts, 65536, async_ctas=1)
+    img = snap.HostBuffer(s.image_bytes(snap.FULL))
+    s.checkpoint_async(img, snap.FULL)
+    s.close()  # no wait: destroy synchronises the background stream
+    s = make_set(ts, 65536)
+    used = s.checkpoint(img, snap.FULL)
+    assert np.array_equal(img.view(used), oracle.write_full(hs, 65536, 0)[1])
+    s.restore_async(img, [1])
+    s.close()  # no restore_wait
+    torch.cuda.synchronize()
+    for a, b in zip(readback(ts), hs):
+        assert np.array_equal(a, b)
