@@ -622,3 +622,69 @@ def test_tma_hash_staging_parity(C):
     assert nd == len(set(dirty)) and np.array_equal(patch.view(used_p), exp)
     assert s.verify(patch, used_p) == 0
     s.close()
+
+
+def test_config3_20gib_sampled_parity():
+    """The 20 GiB state of 2,000 allocations at full size, pipelined: sampled
+    chunks of the full image and of a 1 % clustered patch against the oracle
+    (bytes and CRCs), the patch's dirty set equal to the mutation set, and
+    verify clean."""
+    from struct import unpack_from
+    C = 65536
+    sizes = workloads.config3_sizes(1)
+    align = 1 << 20
+    starts, off = [], 0
+    for n in sizes:
+        starts.append(off)
+        off += (n + align - 1) // align * align
+    arena = torch.empty(off, dtype=torch.uint8, device="cuda")
+    for p in range(0, off, 1 << 30):
+        workloads.torch_random_bytes(arena[p: min(off, p + (1 << 30))], 300 + p // (1 << 30))
+    ts = [arena[a: a + n] for a, n in zip(starts, sizes)]
+    s = make_set(ts, C)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(full, snap.FULL)
+    nch = [(n + C - 1) // C for n in sizes]
+    c0 = np.concatenate([[0], np.cumsum(nch)])
+    rng = np.random.default_rng(301)
+    picks = sorted(set(int(x) for x in rng.integers(0, int(c0[-1]), 48)) | {int(c0[-1]) - 1})
+
+    def locate(c):
+        k = int(np.searchsorted(c0, c, side="right") - 1)
+        return k, c - int(c0[k])
+
+    # record offsets of the full image from the closed-form layout
+    rec, o = [], 64
+    for n, k in zip(sizes, nch):
+        rec.append(o)
+        d = (o + 32 + 4 * k + 4095) // 4096 * 4096
+        o = (d + n + 4095) // 4096 * 4096
+    for c in picks:
+        k, i = locate(c)
+        lo, hi = i * C, min((i + 1) * C, sizes[k])
+        data = ts[k][lo:hi].cpu().numpy()
+        d_off = unpack_from("<Q", full.array, rec[k] + 16)[0]
+        assert np.array_equal(full.array[d_off + lo: d_off + hi], data), c
+        assert unpack_from("<I", full.array, rec[k] + 32 + 4 * i)[0] == oracle.crc32c(data), c
+    # 1 % clustered mutation, pipelined incremental
+    units = workloads.mutation_units(int(c0[-1]), 0.01, 302)
+    muts = [locate(int(u)) for u in units]
+    mutate(ts, C, muts, seed=303)
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    used_p = s.checkpoint(patch, snap.INCREMENTAL)
+    assert s.stats()["dirty_chunks"] == len(units)
+    by_alloc = {}
+    for k, i in muts:
+        by_alloc.setdefault(k, []).append(i)
+    for k in sorted(set(k for k, _ in muts))[:40]:
+        rc, idx = oracle.patch_dirty(patch.view(used_p), k)
+        assert rc == 0 and sorted(idx.tolist()) == sorted(by_alloc[k]), k
+    assert s.verify(patch, used_p) == 0
+    # apply on the host and compare sampled mutated chunks
+    merged = full.view(used).copy()
+    snap.apply_patch(merged, patch.view(used_p))
+    for k, i in muts[:: max(1, len(muts) // 40)]:
+        lo, hi = i * C, min((i + 1) * C, sizes[k])
+        d_off = unpack_from("<Q", merged, rec[k] + 16)[0]
+        assert np.array_equal(merged[d_off + lo: d_off + hi], ts[k][lo:hi].cpu().numpy()), (k, i)
+    s.close()
