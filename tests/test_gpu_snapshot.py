@@ -688,3 +688,59 @@ def test_config3_20gib_sampled_parity():
         d_off = unpack_from("<Q", merged, rec[k] + 16)[0]
         assert np.array_equal(merged[d_off + lo: d_off + hi], ts[k][lo:hi].cpu().numpy()), (k, i)
     s.close()
+
+
+def test_config4_llama7b_state_full_size_sampled_parity():
+    """The Llama-7B-shaped state at full size (1,196 allocations,
+    115,812,655,104 B) through the 4 GiB pinned ring into a pageable image,
+    then restored into freshly allocated buffers: sampled chunks of the image
+    (bytes and CRCs) and of the restored state against the oracle, and verify
+    clean."""
+    import mmap
+    from struct import unpack_from
+    spec = workloads.llama7b_state_spec()
+    sizes = workloads.spec_bytes(spec)
+    need = sum(sizes)
+    free_host = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    free_dev = torch.cuda.mem_get_info()[0]
+    if free_host < need + (24 << 30) or free_dev < need + (8 << 30):
+        pytest.skip("needs %d B of host and device memory" % need)
+    C = 65536
+    ts = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+    workloads.torch_fill_spec(ts, spec, seed=7)
+    s = make_set(ts, C, ring_bytes=4 << 30)
+    nimg = s.image_bytes(snap.FULL)
+    m = mmap.mmap(-1, nimg, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS | getattr(mmap, "MAP_POPULATE", 0))
+    img = np.frombuffer(m, dtype=np.uint8)
+    used = s.checkpoint(img, snap.FULL)
+    nch = [(n + C - 1) // C for n in sizes]
+    c0 = np.concatenate([[0], np.cumsum(nch)])
+    rng = np.random.default_rng(401)
+    picks = sorted(set(int(x) for x in rng.integers(0, int(c0[-1]), 40)) | {int(c0[-1]) - 1, 0})
+    samples = []
+    for c in picks:
+        k = int(np.searchsorted(c0, c, side="right") - 1)
+        i = c - int(c0[k])
+        lo, hi = i * C, min((i + 1) * C, sizes[k])
+        samples.append((k, i, lo, hi, ts[k][lo:hi].cpu().numpy()))
+    rec, o = [], 64
+    for n, k in zip(sizes, nch):
+        rec.append(o)
+        d = (o + 32 + 4 * k + 4095) // 4096 * 4096
+        o = (d + n + 4095) // 4096 * 4096
+    for k, i, lo, hi, data in samples:
+        d_off = unpack_from("<Q", m, rec[k] + 16)[0]
+        assert bytes(img[d_off + lo: d_off + hi]) == data.tobytes(), (k, i)
+        assert unpack_from("<I", m, rec[k] + 32 + 4 * i)[0] == oracle.crc32c(data), (k, i)
+    s.close()
+    del ts
+    torch.cuda.empty_cache()
+    fresh = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
+    s = make_set(fresh, C, ring_bytes=4 << 30)
+    s.restore(img, used)
+    for k, i, lo, hi, data in samples:
+        assert np.array_equal(fresh[k][lo:hi].cpu().numpy(), data), (k, i)
+    assert s.verify(img, used) == 0
+    s.close()
+    del img
+    m.close()
