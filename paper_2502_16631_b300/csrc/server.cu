@@ -462,7 +462,8 @@ size_t count_ready(const snap_server_s *sv)
     return n + std::min<size_t>(need_slot, sv->free_slots.size());
 }
 
-// Fill one round with ready windows, round-robin over the active requests.
+// Fill one round with ready windows: one window per request per pass over
+// the active requests, which the scheduler keeps shortest-remaining first.
 bool build_round(snap_server_s *sv, Round &rd)
 {
     rd.wins.clear();
@@ -590,6 +591,17 @@ void scheduler(snap_server_s *sv)
                 }
             }
         }
+        // Shortest remaining work first: requests nearer completion get the
+        // staging slots and the round places first, so they leave sooner and
+        // fewer requests share the link at any time.  Requests still hashing
+        // or quiescing are ranked by their size in 64 MiB windows.
+        std::stable_sort(sv->active.begin(), sv->active.end(), [](const SReq *x, const SReq *y) {
+            const uint64_t rx = x->wins.size() - std::min<uint64_t>(x->wins.size(), x->done_w);
+            const uint64_t ry = y->wins.size() - std::min<uint64_t>(y->wins.size(), y->done_w);
+            const uint64_t kx = x->phase == P_WINDOWS ? 2 * rx + 1 : x->set->total_bytes >> 26;
+            const uint64_t ky = y->phase == P_WINDOWS ? 2 * ry + 1 : y->set->total_bytes >> 26;
+            return kx < ky;
+        });
         // restore fills need slots before their windows can launch
         for (SReq *r : sv->active) {
             if (r->phase != P_WINDOWS || r->kind != SNAP_REQ_RESTORE) continue;
