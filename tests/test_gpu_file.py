@@ -163,3 +163,35 @@ def test_file_gpt2_state_roundtrip(tmp_path):
         assert np.array_equal(a, b)
     s.close()
     os.unlink(path)
+
+
+_FSIZE_CHILD = r'''
+import os, resource, signal, sys
+sys.path.insert(0, os.environ["SNAP_REPO"])
+import numpy as np, torch
+import paper_2502_16631_b300 as snap
+path = sys.argv[1]
+ts = [torch.ones(3 << 20, dtype=torch.uint8, device="cuda"), torch.ones(5 << 20, dtype=torch.uint8, device="cuda")]
+s = snap.Set(chunk_bytes=65536)
+for t in ts:
+    s.register(t)
+s.prepare(ring=True)
+signal.signal(signal.SIGXFSZ, signal.SIG_IGN)          # a write past the limit fails with EFBIG
+resource.setrlimit(resource.RLIMIT_FSIZE, (1 << 20, 1 << 20))
+rc, _ = s.checkpoint_file_status(path, snap.FULL)
+print(rc, os.path.exists(path), os.path.exists(path + ".tmp"))
+'''
+
+
+def test_file_write_failure_is_eio_and_leaves_nothing(tmp_path):
+    """Storage that refuses the image (a 1 MiB file-size limit in a child
+    process): SNAP_EIO, no file under the name, no temporary file left."""
+    import subprocess
+    import sys
+    path = str(tmp_path / "big.img")
+    env = dict(os.environ, SNAP_REPO=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    r = subprocess.run([sys.executable, "-c", _FSIZE_CHILD, path], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    rc, exists, tmp_exists = r.stdout.split()[-3:]
+    assert int(rc) == snap.EIO and exists == "False" and tmp_exists == "False"
