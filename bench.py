@@ -200,13 +200,24 @@ def link_peak(torch, nbytes=1 * GiB, reps=5):
     return out
 
 
+def kernel_source_key(path: str) -> str:
+    """sha256[:16] of a CUDA source with comments and whitespace removed: the
+    key under which measured counters stay valid (a comment edit keeps it)."""
+    import re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return hashlib.sha256("".join(src.split()).encode()).hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, valid
-    only while the kernel source is unchanged since the capture."""
+    only while the kernel source (its code, not its comments) is unchanged
+    since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = os.path.join(ROOT, "paper_2502_16631_b300", "csrc", "kernels.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_key(src)
         for line in open(path):
             parts = line.split()
             if len(parts) >= 4 and parts[0] == kernel and parts[3] == sha:

@@ -10,8 +10,10 @@
 //   OP_GATHER        TMA bulk copy HBM -> shared memory in 32*P-byte stages,
 //                    CRC-32C from shared memory, 128-bit stores to the mapped
 //                    host image (the device -> host link is the bound);
-//   OP_HASH/VERIFY   128-bit cp.async staging of lane-contiguous segments in
-//                    a padded, bank-conflict-free layout, CRC-32C per lane,
+//   OP_HASH/VERIFY   staging of lane-contiguous segments in an XOR-swizzled,
+//                    bank-conflict-free layout (128-bit cp.async by every
+//                    lane, or one 2D TMA tensor copy per stage whose hardware
+//                    swizzle is the same layout), CRC-32C per lane,
 //                    warp-shuffle combine through GF(2) shift constants (HBM
 //                    read is the bound);
 //   OP_GATHER_DIRTY  the gather path without hashing, into patch slots;
