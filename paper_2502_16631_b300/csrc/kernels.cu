@@ -684,6 +684,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
         v = __shfl_sync(0xFFFFFFFFu, v, 0);
         if (v >= (grp ? tot_b : tot_a)) {
             if (grp) done_b = true; else done_a = true;
+            // every tile of this launch is taken: a launch queued behind it
+            // with programmatic stream serialization (which reads nothing
+            // this one writes) may now take the SMs its CTAs free
+            if (done_a && done_b && lane == 0) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
             continue;
         }
         const unsigned long long t = grp ? tot_a + v : v;
@@ -792,7 +796,7 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
 
 cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigned long long *cursor_a,
                           unsigned long long *cursor_b, const CombineConsts &cc, const TileShape &sh, Result *kres,
-                          cudaStream_t st)
+                          cudaStream_t st, bool overlap_prev)
 {
     const size_t smem = tile_smem_bytes(sh);
     // more than kMaxWarps warps selects the hash/verify-only kernel
@@ -801,6 +805,26 @@ cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigne
     if (n_jobs_a < 0 || n_jobs_a > n_jobs || (n_jobs_a < n_jobs && !cursor_b)) return cudaErrorInvalidValue;
     if (sh.chains < 1 || sh.chains > 2 || sh.stages < 1 || sh.piece < 32 || sh.piece > 256 || (sh.piece & 15))
         return cudaErrorInvalidValue;
+    if (overlap_prev) {
+        // programmatic stream serialization: this launch's CTAs may start
+        // once every CTA of the previous kernel on `st` has run out of
+        // tiles, i.e. in that kernel's tail
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)sh.ctas);
+        cfg.blockDim = dim3((unsigned)sh.warps * 32u);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at{};
+        at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at.val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        if (sh.warps > kMaxWarps)
+            return cudaLaunchKernelEx(&cfg, snap_tiles<true>, jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
+                                      sh.stages, sh.piece, sh.chains, sh.tma, kres);
+        return cudaLaunchKernelEx(&cfg, snap_tiles<false>, jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
+                                  sh.stages, sh.piece, sh.chains, sh.tma, kres);
+    }
     if (sh.warps > kMaxWarps)
         snap_tiles<true><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
                                                                sh.stages, sh.piece, sh.chains, sh.tma, kres);
@@ -811,9 +835,9 @@ cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigne
 }
 
 cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor, const CombineConsts &cc,
-                         const TileShape &sh, Result *kres, cudaStream_t st)
+                         const TileShape &sh, Result *kres, cudaStream_t st, bool overlap_prev)
 {
-    return launch_tiles2(jobs_dev, n_jobs, n_jobs, cursor, nullptr, cc, sh, kres, st);
+    return launch_tiles2(jobs_dev, n_jobs, n_jobs, cursor, nullptr, cc, sh, kres, st, overlap_prev);
 }
 
 // Opt the kernel into the full shared-memory carve-out; call once per

@@ -197,33 +197,51 @@ static void free_device(snap_set_s *s)
     lazy_free_layout(s);
 }
 
-// Groups of whole allocations, in registration order, of about equal bytes
-// for the pipelined incremental checkpoint (one group: no pipeline).  A
-// group holds at least 64 MiB and 4,096 chunks: each group's dirty chunks
-// are gathered by a few warps, one chunk per warp at a time, so a group
-// with only a handful of dirty (large) chunks would leave the link idle.
+// Stage count a pipelined incremental checkpoint of this state aims at:
+// one stage per max(64 MiB, 4,096 chunks) of state, at most kMaxGroups
+// (each stage's dirty chunks are gathered by a few warps, one chunk per
+// warp at a time, so a stage with only a handful of dirty chunks would
+// leave the link idle); fewer than 2: no pipeline.
 static void plan_groups(snap_set_s *s)
 {
     const uint64_t kGroupBytes = std::max<uint64_t>(64ull << 20, 4096 * s->C);
+    s->n_groups = (int)std::min<uint64_t>((uint64_t)kMaxGroups, s->total_bytes / kGroupBytes);
+}
+
+// The stages of a pipelined incremental checkpoint for hash launches of W
+// warps (a warp hashes one chunk at a time).  Every launch but the last
+// hashes a whole number of waves (multiples of W chunks), so that its warps
+// run out of tiles together and no launch ends in a part-filled wave; the
+// last hashes one wave plus the part-filled rest, which keeps the final
+// stage (whose gather nothing overlaps) short.  Allocation group g is the
+// allocations whose last chunk launch g hashes, a zero-byte allocation
+// going with the one before it; a group is empty where one allocation
+// spans several launches.  Returns the launch count (below 2: no pipeline).
+static int plan_pipeline(snap_set_s *s, uint64_t W)
+{
+    const uint64_t N = s->n_chunks;
+    const uint64_t waves = W ? N / W : 0;
+    if (s->n_groups < 2 || waves < 2) return s->n_pipe = 1;
+    const uint64_t H = std::min<uint64_t>({(uint64_t)s->n_groups, waves, (uint64_t)kMaxPipe});
+    // launches 0 .. H-2 share waves-1 whole waves, the later ones taking
+    // the extra wave where they do not divide evenly
+    const uint64_t base = (waves - 1) / (H - 1), extra = (waves - 1) % (H - 1);
+    s->hb[0] = 0;
+    for (uint64_t h = 0; h + 1 < H; ++h) s->hb[h + 1] = s->hb[h] + (base + (h >= H - 1 - extra ? 1 : 0)) * W;
+    s->hb[H] = N;
     const size_t n = s->desc.size();
-    const int G = (int)std::min<uint64_t>((uint64_t)kMaxGroups, s->total_bytes / kGroupBytes);
-    int g = 0;
+    size_t k = 0;
     s->gal[0] = 0;
     s->gch[0] = 0;
-    if (G >= 2) {
-        uint64_t cum = 0;
-        for (size_t k = 0; k + 1 < n; ++k) {
-            cum += s->desc[k].bytes;
-            if (g + 1 < G && cum * (uint64_t)G >= (uint64_t)(g + 1) * s->total_bytes) {
-                ++g;
-                s->gal[g] = k + 1;
-                s->gch[g] = s->desc[k + 1].chunk0;
-            }
-        }
+    for (uint64_t h = 0; h < H; ++h) {
+        if (h + 1 < H)
+            while (k < n && s->desc[k].chunk0 + (s->desc[k].bytes + s->C - 1) / s->C <= s->hb[h + 1]) ++k;
+        else
+            k = n;
+        s->gal[h + 1] = k;
+        s->gch[h + 1] = k < n ? s->desc[k].chunk0 : N;
     }
-    s->n_groups = g + 1;
-    s->gal[s->n_groups] = n;
-    s->gch[s->n_groups] = s->n_chunks;
+    return s->n_pipe = (int)H;
 }
 
 // The driver's tensor-map encoder, looked up once through the runtime (no
@@ -523,19 +541,21 @@ int async_ctas(const snap_set_s *s)
     return std::max(1, std::min(c, s->sms));
 }
 
-// Pipelined incremental checkpoint.  The hash pass (HBM-bound) of allocation
-// group g+1 runs on all but kPipeGatherCtas SMs while the dirty chunks of
-// group g cross the link (link-bound) on the others: a second stream hashes
-// the groups back to back, and the library stream takes each finished group
-// through diff, layout, metadata and gather.  Groups are whole allocations
+// Pipelined incremental checkpoint.  The hash pass (HBM-bound) runs as H
+// launches on all but kPipeGatherCtas SMs, back to back on a second stream,
+// each launch allowed to start in its predecessor's tail (programmatic
+// stream serialization: it reads nothing the predecessor writes); a third
+// stream takes each launch's completed allocations through diff, layout and
+// metadata, and the library stream gathers their dirty chunks (link-bound)
+// on the other SMs while later launches hash.  Groups are whole allocations
 // in registration order, so the dirty list stays ascending and every offset
 // of the patch is the one the whole-state layout gives: the bytes are those
 // of the unpipelined sequence.  Used only when the image capacity covers the
 // largest possible patch, because a group's bytes are written before later
 // groups are laid out.
-static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEntry **out)
+static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const TileShape &shh, GraphEntry **out)
 {
-    const int G = s->n_groups;
+    const int H = s->n_pipe;
     for (cudaStream_t *p : {&s->st_pipe, &s->st_meta})
         if (!*p) {
             const cudaError_t e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
@@ -544,16 +564,16 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEnt
                 return cuda_status(e);
             }
         }
-    for (int i = 0; i < 2 * G + 1; ++i)
+    for (int i = 0; i < 2 * H + 1; ++i)
         if (!s->ev_pipe[i]) {
             const cudaError_t e = cudaEventCreateWithFlags(&s->ev_pipe[i], cudaEventDisableTiming);
             if (e != cudaSuccess) return cuda_status(e);
         }
     CallBlock &cb = *s->h_cb;
-    for (int g = 0; g < G; ++g) {
+    for (int g = 0; g < H; ++g) {
         Job jh = base_job(s, OP_HASH);
-        jh.tile_begin = s->gch[g];
-        jh.n_tiles = s->gch[g + 1] - s->gch[g];
+        jh.tile_begin = s->hb[g];
+        jh.n_tiles = s->hb[g + 1] - s->hb[g];
         jh.hash_out = s->d_hash[cur];
         cb.jobs[g] = jh;
         Job jg = base_job(s, OP_GATHER_DIRTY);
@@ -564,10 +584,9 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEnt
         jg.patch_data = s->d_patch_data;
         jg.dstart = s->d_dstart;
         jg.cap_exceeded = &s->d_cb->res.cap_exceeded;
-        cb.jobs[G + g] = jg;
+        cb.jobs[H + g] = jg;
     }
-    TileShape shh = s->shape[SHAPE_HASH], shg = s->shape[SHAPE_GATHER];
-    shh.ctas = std::max(1, s->sms - kPipeGatherCtas);
+    TileShape shg = s->shape[SHAPE_GATHER];
     shg.ctas = kPipeGatherCtas;
     const CombineConsts cch = make_combine_consts(s->C, shh.piece);
     const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
@@ -580,40 +599,45 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, GraphEnt
         if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[0], q);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h, s->ev_pipe[0], 0);
         if (e == cudaSuccess) e = launch_stamp(&d->res, TS_DIFF_END, q);  // copy_ms spans the whole pipeline
-        // three streams: h hashes the groups back to back; m takes each
-        // hashed group through diff, layout and metadata (they continue the
-        // running dirty count and patch offset, so they stay in group
-        // order); q gathers each group as soon as its metadata is written
+        // three streams: h hashes launch after launch; m takes each
+        // launch's completed allocations through diff, layout and metadata
+        // (they continue the running dirty count and patch offset, so they
+        // stay in order); q gathers each group once its metadata is written
         cudaStream_t m = s->st_meta;
         if (e == cudaSuccess) e = cudaStreamWaitEvent(m, s->ev_pipe[0], 0);
-        for (int g = 0; g < G && e == cudaSuccess; ++g) {
-            if (s->gch[g + 1] > s->gch[g])
-                e = launch_tiles(d->jobs + g, 1, &d->cursor[g], cch, shh, &d->res, h);
-            if (e == cudaSuccess && g == G - 1) e = launch_stamp(&d->res, TS_HASH_END, h);
+        for (int g = 0; g < H && e == cudaSuccess; ++g) {
+            // the first launch follows the prologue's copy of the call block,
+            // so it waits for it in full
+            e = launch_tiles(d->jobs + g, 1, &d->cursor[g], cch, shh, &d->res, h, g > 0);
+            if (e == cudaSuccess && g == H - 1) e = launch_stamp(&d->res, TS_HASH_END, h);
             if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[1 + g], h);
         }
-        for (int g = 0; g < G && e == cudaSuccess; ++g) {
-            const uint64_t a0 = s->gal[g], na = s->gal[g + 1] - s->gal[g];
+        for (int g = 0; g < H && e == cudaSuccess; ++g) {
+            // m waits for every launch in turn, so group g's metadata runs
+            // after launches 0 .. g have all completed (a launch that started
+            // in its predecessor's tail may complete before it)
             e = cudaStreamWaitEvent(m, s->ev_pipe[1 + g], 0);
-            if (e == cudaSuccess)
-                e = launch_diff_range(curp, prevp, s->gch[g], s->gch[g + 1] - s->gch[g], s->d_blockcnt,
-                                      s->d_blockoff, s->d_dlist, &d->res.n_dirty, &d->gbeg[g], &d->gcnt[g], m);
+            const uint64_t a0 = s->gal[g], na = s->gal[g + 1] - s->gal[g];
+            if (e != cudaSuccess || na == 0) continue;
+            e = launch_diff_range(curp, prevp, s->gch[g], s->gch[g + 1] - s->gch[g], s->d_blockcnt, s->d_blockoff,
+                                  s->d_dlist, &d->res.n_dirty, &d->gbeg[g], &d->gcnt[g], m);
             if (e == cudaSuccess)
                 e = launch_patch_layout_range(s->d_allocs, a0, na, s->C, s->d_dlist, s->d_patch_rec,
                                               s->d_patch_data, s->d_dstart, &d->cp, &d->res, &d->run_off, m);
             if (e == cudaSuccess)
                 e = launch_patch_meta_range(s->d_allocs, a0, na, s->C, curp, s->d_dlist, s->d_patch_rec,
                                             s->d_patch_data, s->d_dstart, &d->res, &d->cp, m);
-            if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[1 + G + g], m);
+            if (e == cudaSuccess) e = cudaEventRecord(s->ev_pipe[1 + H + g], m);
         }
-        for (int g = 0; g < G && e == cudaSuccess; ++g) {
-            e = cudaStreamWaitEvent(q, s->ev_pipe[1 + G + g], 0);
+        for (int g = 0; g < H && e == cudaSuccess; ++g) {
+            if (s->gal[g + 1] == s->gal[g]) continue;
+            e = cudaStreamWaitEvent(q, s->ev_pipe[1 + H + g], 0);
             if (e == cudaSuccess)
-                e = launch_tiles(d->jobs + G + g, 1, &d->cursor[G + g], ccg, shg, &d->res, q);
+                e = launch_tiles(d->jobs + H + g, 1, &d->cursor[H + g], ccg, shg, &d->res, q);
         }
         // join the hash stream too (its last event precedes the last metadata,
         // but a join must name the stream's own last work)
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(q, s->ev_pipe[G], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(q, s->ev_pipe[H], 0);
         if (e == cudaSuccess) e = enqueue_epilogue(s, q);
         return e;
     }, out);
@@ -648,7 +672,12 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
             return e;
         }, out);
     }
-    if (!from_shadow && s->n_groups >= 2 && cap >= s->patch_bound) return pipelined_incremental(s, cur, dimg, out);
+    if (!from_shadow && s->n_groups >= 2 && cap >= s->patch_bound) {
+        TileShape shp = shh;
+        shp.ctas = std::max(1, s->sms - kPipeGatherCtas);
+        if (plan_pipeline(s, (uint64_t)shp.ctas * (uint64_t)shp.warps) >= 2)
+            return pipelined_incremental(s, cur, dimg, shp, out);
+    }
     Job jh = base_job(s, OP_HASH);
     jh.allocs = allocs;
     jh.hash_out = s->d_hash[cur];

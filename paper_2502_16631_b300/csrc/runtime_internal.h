@@ -19,9 +19,11 @@ struct ImageHeader {
     uint64_t chunk_bytes, n_allocs, total, generation, parent;
 };
 
-// A pipelined incremental checkpoint splits the allocations into at most
-// this many groups (whole allocations, in registration order).
+// A pipelined incremental checkpoint aims at about this many stages (hash
+// launches of equal whole waves of tiles; the allocations each completes),
+// and has at most kMaxPipe.
 constexpr int kMaxGroups = 16;
+constexpr int kMaxPipe = 2 * kMaxGroups;
 // CTAs that gather dirty chunks while the other SMs hash the next group: the
 // device-to-host link saturates with 8 gather CTAs on B300.
 constexpr int kPipeGatherCtas = 8;
@@ -29,9 +31,9 @@ constexpr int kPipeGatherCtas = 8;
 // Everything one launch sequence needs that changes from call to call; the
 // host fills a pinned copy and the captured graph's first node copies it in.
 struct CallBlock {
-    unsigned long long cursor[2 * kMaxGroups + 2];  // tile cursors of the sequence's launches
-    unsigned long long gbeg[kMaxGroups];            // pipelined incremental: each group's
-    unsigned long long gcnt[kMaxGroups];            //   dirty-list range
+    unsigned long long cursor[2 * kMaxPipe + 2];  // tile cursors of the sequence's launches
+    unsigned long long gbeg[kMaxPipe];             // pipelined incremental: each group's
+    unsigned long long gcnt[kMaxPipe];             //   dirty-list range
     unsigned long long run_off;                     //   and the running patch offset
     Result res;
     CallParams cp;
@@ -90,12 +92,16 @@ struct snap_set_s {
     uint64_t base_gen = 0;
     uint64_t next_gen = 0;
 
-    // pipelined incremental: allocation groups [gal[g], gal[g+1]) covering
-    // chunks [gch[g], gch[g+1]); a second stream and its fork/join events
-    int n_groups = 0;
-    uint64_t gal[snapk::kMaxGroups + 1] = {}, gch[snapk::kMaxGroups + 1] = {};
+    // pipelined incremental: n_groups = the stage count the state's bytes
+    // call for (2 or more: pipelined); at capture, n_pipe hash launches over
+    // chunks [hb[g], hb[g+1]), and allocation groups [gal[g], gal[g+1])
+    // (chunks [gch[g], gch[g+1])) = the allocations launch g completes;
+    // two more streams and their fork/join events
+    int n_groups = 0, n_pipe = 0;
+    uint64_t hb[snapk::kMaxPipe + 1] = {};
+    uint64_t gal[snapk::kMaxPipe + 1] = {}, gch[snapk::kMaxPipe + 1] = {};
     cudaStream_t st_pipe = nullptr, st_meta = nullptr;
-    cudaEvent_t ev_pipe[2 * snapk::kMaxGroups + 1] = {};
+    cudaEvent_t ev_pipe[2 * snapk::kMaxPipe + 1] = {};
 
     std::vector<snapk::GraphEntry> graphs;
     snapk::TileShape shape[snapk::SHAPE_COUNT];

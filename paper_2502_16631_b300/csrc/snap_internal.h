@@ -122,14 +122,17 @@ size_t tile_smem_bytes(const TileShape &sh);
 constexpr size_t kMaxSmem = 232448;  // 227 KiB opt-in per CTA
 
 // Kernel launchers.  All run on `st`.
+// `overlap_prev`: launched with programmatic stream serialization, so its
+// CTAs may start while the previous tile kernel on `st` finishes its last
+// tiles; only for a launch that reads nothing the previous one writes.
 cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor,
                          const CombineConsts &cc, const TileShape &sh, Result *kres,
-                         cudaStream_t st);
+                         cudaStream_t st, bool overlap_prev = false);
 // Two job groups with their own cursors: jobs [0, n_jobs_a) (device to
 // host) and [n_jobs_a, n_jobs) (host to device), worked on concurrently.
 cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigned long long *cursor_a,
                           unsigned long long *cursor_b, const CombineConsts &cc, const TileShape &sh, Result *kres,
-                          cudaStream_t st);
+                          cudaStream_t st, bool overlap_prev = false);
 CombineConsts make_combine_consts(uint64_t chunk_bytes, int piece);
 cudaError_t init_tile_kernel();
 cudaError_t launch_full_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes,
