@@ -441,7 +441,7 @@ def _pipeline_state(seed):
     """About 630 MiB in 41 allocations of uneven sizes (zero bytes, a few
     bytes, ragged, one of 200 MiB): two hash launches of the pipelined
     incremental at 64 KiB chunks, nine at 16 KiB, where the 200 MiB
-    allocation spans three launches and leaves one allocation group empty
+    allocation spans several launches and leaves one allocation group empty
     (with the default 24-warp hash shape on 140 SMs)."""
     rng = np.random.default_rng(seed)
     sizes = [int(x) for x in rng.integers(1, 24 * MiB, 36)] + [0, 17, 200 * MiB + 12345, 65536, 3]
