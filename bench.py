@@ -449,6 +449,29 @@ def run_snap(args, rank, world, local, pg):
     total_bytes = reduce_sum(pg, 4.0 * B)
     value = total_bytes / (ms_max * 1e-3) / 1e9
 
+    # the same step with ordinary pageable images (numpy arrays): the library
+    # streams them through its pinned ring, host copies included
+    pg_full = np.empty(full.nbytes, np.uint8)
+    pg_patch = np.empty(patch.nbytes, np.uint8)
+
+    def step_pageable():
+        uf = s.checkpoint(pg_full, snap.FULL)
+        grid[units] ^= masks
+        up = s.checkpoint(pg_patch, snap.INCREMENTAL)
+        bad = s.verify(pg_patch, up)
+        s.restore(pg_full, uf)
+        if bad != 0:
+            raise RuntimeError("verify against the pageable patch found %d mismatches" % bad)
+    step_pageable()
+    torch.cuda.synchronize()
+    n_pageable = 3
+    h2 = time.perf_counter()
+    for _ in range(n_pageable):
+        step_pageable()
+    torch.cuda.synchronize()
+    pageable_ms = (time.perf_counter() - h2) * 1e3 / n_pageable
+    del pg_full, pg_patch
+
     # plain form (one cudaMemcpyAsync per allocation, full copy every time)
     plain_c, plain_r = [], []
     for _ in range(3):
@@ -516,6 +539,10 @@ def run_snap(args, rank, world, local, pg):
                 "d2h_bytes_per_step": used_full + used_patch,
                 "note": "host wall clock around the public API calls of the step (Python binding -> C ABI "
                         "-> graph launch -> completion), images in pinned host memory"},
+        "e2e_pageable": {"value": total_bytes / (reduce_max(pg, pageable_ms) * 1e-3) / 1e9, "unit": "GB/s",
+                         "steps": n_pageable,
+                         "note": "the same step with numpy (pageable) images, streamed through the library's "
+                                 "pinned ring with host copies; host wall clock"},
         "gpu_launches": counts["kernels"],
         "clocks": clk,
     }
