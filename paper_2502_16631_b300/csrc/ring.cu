@@ -237,6 +237,15 @@ uint64_t parts_for(uint64_t bytes, int threads)
     return std::min<uint64_t>(p, (uint64_t)threads * 2);
 }
 
+// Window size of a ring transfer: at most a slot, and about 1/32 of the
+// state (at least 16 MiB), so that the first window's gather (or fill) and
+// the last window's host copy, which nothing overlaps, stay short.
+static uint64_t ring_window_bytes(const snap_set_s *s, const Ring *r)
+{
+    const uint64_t target = std::max<uint64_t>(16ull << 20, (s->total_bytes / 32 + 4095u) & ~uint64_t(4095u));
+    return std::max<uint64_t>(s->C, std::min<uint64_t>(r->slot_bytes, target));
+}
+
 // Kernels this call launched may still be running after an error: the next
 // call on the set waits for them (bounded) before it reuses the ring.
 static void mark_in_flight(snap_set_s *s)
@@ -257,7 +266,7 @@ static void drain(Progress &pg)
 static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double deadline, int cur, snap_stats &st)
 {
     if (cap < s->full_bytes) return SNAP_EINVAL;
-    const std::vector<Window> win = make_windows(s, r->slot_bytes);
+    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r));
     const size_t W = win.size();
     Progress pg;
     pg.left.assign(W, 0);
@@ -396,8 +405,12 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
         io.zero(z, pdat[k] - z);
     }
     if (io.err) return io.err;
-    // dirty data: windows of whole C-byte slots over the dirty ranks
-    const uint64_t per = r->slot_bytes / s->C;
+    // dirty data: windows of whole C-byte slots over the dirty ranks, about
+    // as many windows as the ring has slots (at least 2 MiB each) so that
+    // the host copies of one window overlap the gathers of the next
+    const uint64_t per_slot = r->slot_bytes / s->C;
+    const uint64_t per = std::max<uint64_t>(1, std::min<uint64_t>(
+        per_slot, std::max<uint64_t>((nd + r->slots - 1) / (uint64_t)r->slots, (2ull << 20) / s->C)));
     const size_t W = (size_t)((nd + per - 1) / per);
     Progress pg;
     pg.left.assign(W, 0);
@@ -429,32 +442,38 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
             rc = cuda_status(e);
             break;
         }
+        // the window's chunks are copied out by up to 2 x threads parts of
+        // at least 1 MiB each, so the last window's copy is short too
+        const uint64_t np = std::min<uint64_t>({r1 - r0, (uint64_t)r->pool->size() * 2,
+                                                std::max<uint64_t>(1, (r1 - r0) * s->C >> 20)});
         {
             std::lock_guard<std::mutex> lk(pg.mu);
-            pg.left[w] = 1;
-            pg.outstanding += 1;
+            pg.left[w] = (int)np;
+            pg.outstanding += (int)np;
         }
-        r->pool->push([&, w, slot, r0, r1] {
-            if (!pg.err) {
-                const int q = wait_event(r->ev[slot], deadline);
-                if (q) pg.err = q;
-            }
-            if (!pg.err) {
-                const uint8_t *sl = r->host + (uint64_t)slot * r->slot_bytes;
-                size_t k = 0;
-                for (uint64_t q = r0; q < r1; ++q) {
-                    const uint64_t c = dl[q];
-                    while (k + 1 < na && s->desc[k + 1].chunk0 <= c) ++k;
-                    while (k > 0 && s->desc[k].chunk0 > c) --k;
-                    const AllocDesc &a = s->desc[k];
-                    const uint64_t i = c - a.chunk0;
-                    const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
-                    io.put(pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
+        for (uint64_t p = 0; p < np; ++p) {
+            const uint64_t q0 = r0 + (r1 - r0) * p / np, q1 = r0 + (r1 - r0) * (p + 1) / np;
+            r->pool->push([&, w, slot, r0, q0, q1] {
+                if (!pg.err) {
+                    const int q = wait_event(r->ev[slot], deadline);
+                    if (q) pg.err = q;
                 }
-                if (io.err) pg.err = SNAP_EIO;
-            }
-            pg.done(w);
-        });
+                if (!pg.err) {
+                    const uint8_t *sl = r->host + (uint64_t)slot * r->slot_bytes;
+                    // allocation of the part's first dirty chunk, then forward
+                    size_t k = (size_t)(std::upper_bound(dst.begin(), dst.begin() + na, q0) - dst.begin()) - 1;
+                    for (uint64_t q = q0; q < q1; ++q) {
+                        while (k + 1 < na && dst[k + 1] <= q) ++k;
+                        const AllocDesc &a = s->desc[k];
+                        const uint64_t i = dl[q] - a.chunk0;
+                        const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
+                        io.put(pdat[k] + (q - dst[k]) * s->C, sl + (q - r0) * s->C, upg(L));
+                    }
+                    if (io.err) pg.err = SNAP_EIO;
+                }
+                pg.done(w);
+            });
+        }
     }
     drain(pg);
     if (rc == SNAP_OK && pg.err) rc = pg.err;
@@ -518,7 +537,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
     int rc = ring_get(s, &r);
     if (rc) return rc;
     const int cur = 1 - s->prev_idx;
-    const std::vector<Window> win = make_windows(s, r->slot_bytes);
+    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r));
     const size_t W = win.size();
     Progress pg;
     pg.left.assign(W, 0);

@@ -296,6 +296,31 @@ def test_ring_pageable_images(C, ring):
     assert s.committed_hashes(sum(nch))[1] == 0
 
 
+def test_ring_pageable_incremental_many_windows():
+    """A patch of thousands of dirty chunks into a pageable image: the ring
+    path cuts the dirty ranks into one window per slot (16 here), each copied
+    out by parallel parts of about 1 MiB; every third allocation has no dirty
+    chunk, so parts start and end inside and between allocations."""
+    C = 65536
+    sizes, ts = _pipeline_state(53)
+    s = make_set(ts, C, ring_bytes=1 << 30)
+    full = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
+    s.checkpoint(full, snap.FULL)
+    base = readback(ts)
+    nch = [(n + C - 1) // C for n in sizes]
+    rng = np.random.default_rng(54)
+    dirty = sorted((k, i) for k, n in enumerate(nch) if k % 3 for i in range(n) if rng.random() < 0.7)
+    assert len(dirty) > 4096  # windows of more than 16 MiB
+    mutate(ts, C, dirty, seed=55)
+    cur = readback(ts)
+    patch = np.full(s.image_bytes(snap.INCREMENTAL), 0x5A, dtype=np.uint8)
+    used = s.checkpoint(patch, snap.INCREMENTAL)
+    rc, exp, nd = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in base], 1, 0)
+    assert rc == 0 and nd == len(dirty) and s.stats()["dirty_chunks"] == nd
+    assert used == exp.size and np.array_equal(patch[:used], exp)
+    s.close()
+
+
 # ------------------------------------------------------------- autotuner
 @pytest.mark.parametrize("C", [4096, 65536])
 def test_autotune_every_shape_agrees_then_parity(C):
