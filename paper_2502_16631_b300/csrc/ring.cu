@@ -405,12 +405,15 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
         io.zero(z, pdat[k] - z);
     }
     if (io.err) return io.err;
-    // dirty data: windows of whole C-byte slots over the dirty ranks, about
-    // as many windows as the ring has slots (at least 2 MiB each) so that
-    // the host copies of one window overlap the gathers of the next
+    // dirty data: windows of whole C-byte slots over the dirty ranks; into
+    // memory about as many windows as the ring has slots (at least 2 MiB
+    // each) so that the host copies of one window overlap the gathers of the
+    // next, into a file whole slots (one sequential writer per window)
     const uint64_t per_slot = r->slot_bytes / s->C;
-    const uint64_t per = std::max<uint64_t>(1, std::min<uint64_t>(
-        per_slot, std::max<uint64_t>((nd + r->slots - 1) / (uint64_t)r->slots, (2ull << 20) / s->C)));
+    const uint64_t per = io.mem ? std::max<uint64_t>(1, std::min<uint64_t>(per_slot,
+                                      std::max<uint64_t>((nd + r->slots - 1) / (uint64_t)r->slots,
+                                                         (2ull << 20) / s->C)))
+                                : per_slot;
     const size_t W = (size_t)((nd + per - 1) / per);
     Progress pg;
     pg.left.assign(W, 0);
@@ -442,10 +445,12 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
             rc = cuda_status(e);
             break;
         }
-        // the window's chunks are copied out by up to 2 x threads parts of
-        // at least 1 MiB each, so the last window's copy is short too
-        const uint64_t np = std::min<uint64_t>({r1 - r0, (uint64_t)r->pool->size() * 2,
-                                                std::max<uint64_t>(1, (r1 - r0) * s->C >> 20)});
+        // into memory the window's chunks are copied out by up to 2 x threads
+        // parts of at least 1 MiB each, so the last window's copy is short
+        // too; into a file one writer per window
+        const uint64_t np = io.mem ? std::min<uint64_t>({r1 - r0, (uint64_t)r->pool->size() * 2,
+                                                         std::max<uint64_t>(1, (r1 - r0) * s->C >> 20)})
+                                   : 1;
         {
             std::lock_guard<std::mutex> lk(pg.mu);
             pg.left[w] = (int)np;
