@@ -70,7 +70,8 @@ def parse():
                    "library default, which gives the reported value)")
     p.add_argument("--arrivals", type=int, default=1200, help="serving: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
-    p.add_argument("--serve-pool-gib", type=int, default=8, help="serving: pinned staging pool (GiB)")
+    p.add_argument("--serve-pool-gib", type=int, default=24, help="serving: pinned staging pool (GiB, within "
+                   "the 64 GB pinned budget)")
     p.add_argument("--no-plain", action="store_true", help="serving: skip the serial plain-copy comparison")
     return p.parse_args()
 
