@@ -296,6 +296,27 @@ def test_ring_pageable_images(C, ring):
     assert s.committed_hashes(sum(nch))[1] == 0
 
 
+def test_ring_pageable_windows_smaller_than_slots():
+    """A 640 MiB state through a 4 GiB ring: windows of about 20 MiB (1/32
+    of the state) in 256 MiB slots, 32 or more of them, so the 16 slots are
+    reused; the pageable full image equals the oracle's and the restore from
+    it brings every byte back."""
+    C = 65536
+    sizes, ts = _pipeline_state(57)
+    s = make_set(ts, C, ring_bytes=4 << 30)
+    full = np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8)
+    base = readback(ts)
+    used = s.checkpoint(full, snap.FULL)
+    rc, exp = oracle.write_full(base, C, 0)
+    assert rc == 0 and used == exp.size and np.array_equal(full[:used], exp)
+    for t in ts:
+        t.zero_()
+    s.restore(full, used)
+    for a, b in zip(readback(ts), base):
+        assert np.array_equal(a, b)
+    s.close()
+
+
 def test_ring_pageable_incremental_many_windows():
     """A patch of thousands of dirty chunks into a pageable image: the ring
     path cuts the dirty ranks into one window per slot (16 here), each copied
