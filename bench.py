@@ -201,6 +201,30 @@ def link_peak(torch, nbytes=1 * GiB, reps=5):
     return out
 
 
+def link_peak_both(torch, nbytes=1 * GiB, reps=3):
+    """Both link directions at once (the serving loop's case): copy engines on
+    two streams, and SM loads/stores with half the warps each way; GB/s of
+    the two directions' bytes together."""
+    import paper_2502_16631_b300 as snap
+    d1 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h1 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    best = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            h1.copy_(d1, non_blocking=True)
+        with torch.cuda.stream(s2):
+            d2.copy_(h2, non_blocking=True)
+        torch.cuda.synchronize()
+        best = max(best, 2 * nbytes / (time.perf_counter() - t0) / 1e9)
+    del d1, d2, h1, h2
+    return {"ce_both": best, "sm_both": snap.link_ceiling(2, nbytes, 3)}
+
+
 def kernel_source_key(path: str) -> str:
     """sha256[:16] of a CUDA source with comments and whitespace removed: the
     key under which measured counters stay valid (a comment edit keeps it)."""
@@ -903,6 +927,7 @@ def run_serving(args, rank, world, local, pg):
                      ring_bytes=args.serve_pool_gib * GiB)
     lat = [None] * len(reqs)
     moved = [0] * len(reqs)
+    link = [0] * len(reqs)  # bytes over the host link: image or patch written, or image restored
     status = [0] * len(reqs)
     per_tenant = [[] for _ in T]
     for i, (ta, k, kind) in enumerate(reqs):
@@ -936,6 +961,7 @@ def run_serving(args, rank, world, local, pg):
                 lat[i] = (done - (start + ta)) * 1e3
                 status[i] = st_
                 moved[i] = tk["bytes"]
+                link[i] = int(stats["image_bytes"]) if kind == "incremental" else tk["bytes"]
 
     th = [threading.Thread(target=tenant_loop, args=(k,)) for k in range(len(T))]
     t0 = time.perf_counter()
@@ -947,6 +973,10 @@ def run_serving(args, rank, world, local, pg):
     sv.close()
     good = [l for l, s_ in zip(lat, status) if s_ == 0 and l is not None]
     gbs = sum(m_ for m_, s_ in zip(moved, status) if s_ == 0) / wall / 1e9
+    link_gbs = sum(b_ for b_, s_ in zip(link, status) if s_ == 0) / wall / 1e9
+    offered_gbs = (sum(T[k]["bytes"] for _, k, kind in reqs if kind != "incremental")
+                   + sum(0.05 * T[k]["bytes"] for _, k, kind in reqs if kind == "incremental")) / reqs[-1][0] / 1e9
+    both = link_peak_both(torch)
     # serial plain full copies of the same arrivals (FIFO single server; each
     # request's service time measured by running it, start = max(arrival,
     # previous end)); the first 240 arrivals
@@ -976,6 +1006,13 @@ def run_serving(args, rank, world, local, pg):
                                                  "p99": float(np.percentile(plain_lat, 99)),
                                                  "ours_p50": float(np.percentile(ours_prefix, 50)),
                                                  "ours_p99": float(np.percentile(ours_prefix, 99))} if nb else None),
+                 "roofline": {"bound": "host_link (both directions)", "kernel": "serving rounds (mixed gather + "
+                              "scatter launches) + host copies", "achieved": link_gbs, "peak": both["sm_both"],
+                              "unit": "GB/s", "frac": link_gbs / both["sm_both"], "ce_both": both["ce_both"],
+                              "offered": offered_gbs,
+                              "note": "achieved = image, patch and restore bytes over the link / wall time; peak = "
+                                      "SM loads/stores in both directions at once (snap_link_ceiling 2); offered = "
+                                      "the arrivals' link bytes / arrival span (patches at 5 %)"},
                  "staging_pool_gib": args.serve_pool_gib,
                  "kinds": {k_: sum(1 for _, _, kk in reqs if kk == k_) for k_ in ("full", "incremental", "restore")}})
     print(json.dumps(out))

@@ -308,13 +308,15 @@ SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *
 
 /* Measure the rate at which SM loads and stores move bytes between device
  * memory and pinned, mapped host memory (direction 0: device to host, 1:
- * host to device), best of `reps` launches over `bytes` (a multiple of 8 KiB
- * is used).  This is the ceiling of the gather and scatter kernels, which
- * move the image with SM accesses; on the measured B300 machines every SM store
- * form (16-byte stores, TMA bulk stores, plain load/store) reaches the same
- * rate, below the copy engines'.  Allocates and frees `bytes` of device and
- * pinned host memory.  device -1 = the current device.  Errors: EINVAL,
- * ENOMEM, ECUDA. */
+ * host to device, 2: both at once, half the warps each way; *gbs is then the
+ * two directions' bytes together), best of `reps` launches over `bytes` per
+ * direction (a multiple of 8 KiB is used).  This is the ceiling of the
+ * gather and scatter kernels, which move the image with SM accesses, and
+ * (direction 2) of a launch mixing them; on the measured B300 machines every SM
+ * store form (16-byte stores, TMA bulk stores, plain load/store) reaches the
+ * same rate, below the copy engines'.  Allocates and frees `bytes` (twice
+ * that for direction 2) of device and pinned host memory.  device -1 = the
+ * current device.  Errors: EINVAL, ENOMEM, ECUDA. */
 SNAP_API int snap_link_ceiling(int device, int direction, uint64_t bytes, int reps, double *gbs);
 
 /* ----------------------------------------------------------- autotuning */

@@ -419,7 +419,8 @@ def _agree_callback(agree):
 
 def link_ceiling(direction: int = 0, nbytes: int = 1 << 30, reps: int = 3, device: int = -1) -> float:
     """GB/s that SM loads/stores reach over the host link (0: device to host,
-    1: host to device): the gather and scatter kernels' ceiling."""
+    1: host to device, 2: both at once, the two directions' bytes together):
+    the gather and scatter kernels' ceiling, and a mixed launch's."""
     v = ctypes.c_double()
     _check(_lib().snap_link_ceiling(device, direction, nbytes, reps, ctypes.byref(v)), "snap_link_ceiling")
     return v.value

@@ -472,13 +472,16 @@ def test_gpt2_state_full_parity():
 
 
 def test_link_ceiling_measures_both_directions():
-    """The SM-path ceiling the gather and scatter are held to: positive in both
-    directions; bad arguments are rejected before anything is allocated."""
+    """The SM-path ceiling the gather and scatter are held to: positive in each
+    direction and in both at once (whose combined rate is at least either
+    direction's alone); bad arguments are rejected before anything is
+    allocated."""
     d2h = snap.link_ceiling(0, 256 * MiB, 1)
     h2d = snap.link_ceiling(1, 256 * MiB, 1)
-    assert d2h > 1.0 and h2d > 1.0
+    both = snap.link_ceiling(2, 256 * MiB, 1)
+    assert d2h > 1.0 and h2d > 1.0 and both > 0.9 * max(d2h, h2d)
     v = __import__("ctypes").c_double()
-    assert snap.lib().snap_link_ceiling(-1, 2, 1 << 20, 1, v) == snap.EINVAL
+    assert snap.lib().snap_link_ceiling(-1, 3, 1 << 20, 1, v) == snap.EINVAL
     assert snap.lib().snap_link_ceiling(-1, 0, 4096, 1, v) == snap.EINVAL
     assert snap.lib().snap_link_ceiling(-1, 0, 1 << 20, 0, v) == snap.EINVAL
 
