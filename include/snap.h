@@ -343,7 +343,13 @@ SNAP_API int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap,
 /* A request loop over many tenant sets: requests are admitted as pinned-host
  * and HBM budget frees up, and the chunk tiles of all admitted requests are
  * batched into shared persistent launches (continuous batching), so requests
- * that arrive while others run overlap on the device. */
+ * that arrive while others run overlap on the device.  The server pins a
+ * staging pool of o->ring_bytes (else $SNAP_SERVER_POOL_BYTES, else 8 GiB;
+ * at most pinned_budget) in slots of up to 64 MiB, and runs one host copy
+ * worker per host thread ($SNAP_WORKERS overrides) to move window data
+ * between the pool and the tenants' images.  o may be NULL (chunk_bytes,
+ * timeout_ms and device as for snap_set_create).  Errors: EINVAL (zero
+ * budget, bad chunk size), ENOMEM (pool), ECUDA. */
 SNAP_API int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_budget,
                        const snap_opts *o);
 SNAP_API int snap_server_destroy(snap_server sv);
