@@ -151,6 +151,17 @@ SNAP_API int snap_image_bytes(snap_set s, int mode, uint64_t *out);
 SNAP_API int snap_host_alloc(uint64_t bytes, void **out);
 SNAP_API int snap_host_free(void *p);
 
+/* Pin and map existing host memory [p, p+bytes) -- a caller's own image
+ * buffer -- so that checkpoints, restores and server requests read and
+ * write it directly over the link, as they do snap_host_alloc memory,
+ * instead of staging it through pinned slots and host copies.  The memory
+ * stays the caller's; undo with snap_host_unregister(p) before freeing it.
+ * Pinning costs time in proportion to bytes and counts against the host's
+ * locked memory.  Errors: EINVAL (null, zero bytes, already registered /
+ * not registered), ENOMEM, ECUDA. */
+SNAP_API int snap_host_register(void *p, uint64_t bytes);
+SNAP_API int snap_host_unregister(void *p);
+
 /* --------------------------------------------------------- checkpoint path */
 /* Checkpoint the set into host_image[0..cap) (16-byte aligned).
  *  SNAP_FULL: writes the full image: 64-byte header, then per allocation a
@@ -355,8 +366,11 @@ SNAP_API int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64
 SNAP_API int snap_server_destroy(snap_server sv);
 /* Queue a request on tenant set `tenant` (created on the server's device).
  * kind: SNAP_REQ_FULL / SNAP_REQ_INCREMENTAL write `image` (cap bytes);
- * SNAP_REQ_RESTORE reads it.  *ticket identifies it.  EBUDGET if it can never
- * be admitted under the budgets. */
+ * SNAP_REQ_RESTORE reads it.  An image whose cap bytes lie in one pinned,
+ * mapped region (snap_host_alloc, snap_host_register) is read and written
+ * directly by the kernels and charges no staging; any other image is staged
+ * through the server's pool by its copy workers.  *ticket identifies it.
+ * EBUDGET if it can never be admitted under the budgets. */
 SNAP_API int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, uint64_t cap,
                        uint64_t *ticket);
 /* Wait up to timeout_ms for a ticket; *status gets the request's own status,

@@ -33,7 +33,7 @@ REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 # Every entry point declared in include/snap.h.
 EXPORTS = (
     "snap_set_create", "snap_set_destroy", "snap_set_prepare", "snap_register", "snap_image_bytes",
-    "snap_host_alloc", "snap_host_free", "snap_checkpoint", "snap_checkpoint_async", "snap_checkpoint_wait",
+    "snap_host_alloc", "snap_host_free", "snap_host_register", "snap_host_unregister", "snap_checkpoint", "snap_checkpoint_async", "snap_checkpoint_wait",
     "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
@@ -106,6 +106,8 @@ def _lib():
             "snap_image_bytes": [vp, i32, P(u64)],
             "snap_host_alloc": [u64, P(vp)],
             "snap_host_free": [vp],
+            "snap_host_register": [vp, u64],
+            "snap_host_unregister": [vp],
             "snap_checkpoint": [vp, vp, u64, i32, P(u64)],
             "snap_checkpoint_async": [vp, vp, u64, i32],
             "snap_checkpoint_wait": [vp, u32, P(u64)],
@@ -415,6 +417,17 @@ def _agree_callback(agree):
         except Exception:  # the transport failed: report it as a failure
             return ETIMEDOUT
     return AGREE_FN(f)
+
+
+def host_register(array: np.ndarray) -> None:
+    """Pin and map a caller's host array (snap_host_register) so that calls
+    and server requests use it as an image directly, without staging."""
+    _check(_lib().snap_host_register(array.ctypes.data, array.nbytes), "snap_host_register")
+
+
+def host_unregister(array: np.ndarray) -> None:
+    """Undo host_register (before the array is freed)."""
+    _check(_lib().snap_host_unregister(array.ctypes.data), "snap_host_unregister")
 
 
 def link_ceiling(direction: int = 0, nbytes: int = 1 << 30, reps: int = 3, device: int = -1) -> float:

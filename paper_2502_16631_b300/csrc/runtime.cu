@@ -791,6 +791,25 @@ int snap_host_free(void *p)
     return cuda_status(cudaFreeHost(p));
 }
 
+int snap_host_register(void *p, uint64_t bytes)
+{
+    if (!p || bytes == 0) return SNAP_EINVAL;
+    const cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterMapped | cudaHostRegisterPortable);
+    if (e == cudaSuccess) return SNAP_OK;
+    cudaGetLastError();
+    if (e == cudaErrorHostMemoryAlreadyRegistered || e == cudaErrorInvalidValue) return SNAP_EINVAL;
+    return e == cudaErrorMemoryAllocation ? SNAP_ENOMEM : SNAP_ECUDA;
+}
+
+int snap_host_unregister(void *p)
+{
+    if (!p) return SNAP_EINVAL;
+    const cudaError_t e = cudaHostUnregister(p);
+    if (e == cudaSuccess) return SNAP_OK;
+    cudaGetLastError();
+    return e == cudaErrorHostMemoryNotRegistered || e == cudaErrorInvalidValue ? SNAP_EINVAL : SNAP_ECUDA;
+}
+
 int snap_set_create(snap_set *out, const snap_opts *o)
 {
     if (!out) return SNAP_EINVAL;

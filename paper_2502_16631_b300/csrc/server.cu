@@ -10,8 +10,9 @@
 // the persistent tile kernel (one job per window), so tiles of requests that
 // arrived at different times share the GPU.  Two rounds are kept in flight.
 // Host workers move window data between the server's pinned slots and the
-// tenants' (pageable or pinned) images: slots are filled before a restore
-// window launches and drained after a checkpoint window completes.  When a
+// tenants' pageable images: slots are filled before a restore window
+// launches and drained after a checkpoint window completes.  A pinned,
+// mapped image needs neither: its windows read and write it directly.  When a
 // request's last window is drained its metadata is written, the tenant set
 // commits (exactly as the synchronous calls do) and its waiter is woken;
 // latency is measured from submit to that moment.
@@ -61,6 +62,9 @@ struct SReq {
     snap_set_s *set = nullptr;
     int kind = 0;
     uint8_t *image = nullptr;
+    uint8_t *dimg = nullptr;  // device address of a pinned, mapped image: its
+                              // windows read and write it directly (no slot,
+                              // no host copy); null for a pageable image
     uint64_t cap = 0;
     double t_arrive = 0, t_admit = 0, t_done = 0;
     int status = 1;  // 1 while running
@@ -182,6 +186,7 @@ int prepare(snap_server_s *sv, SReq *r)
         w.c1 = x.c1;
         w.b0 = x.b0;
         w.b1 = x.b1;
+        if (r->dimg) w.state = W_READY;  // direct: nothing to stage
         r->wins.push_back(w);
     }
     if (r->kind == SNAP_REQ_RESTORE && s->n_chunks) {
@@ -253,6 +258,7 @@ int after_hash(snap_server_s *sv, SReq *r)
         w.op = OP_GATHER_DIRTY;
         w.c0 = r0;
         w.c1 = std::min(nd, r0 + per);
+        if (r->dimg) w.state = W_READY;
         r->wins.push_back(w);
     }
     r->phase = P_WINDOWS;
@@ -350,7 +356,9 @@ void admit(snap_server_s *sv)
             ++it;
             continue;
         }
-        const uint64_t pin = std::min<uint64_t>(req_bytes(r), kStagingCap);
+        // staging is charged to pageable images only (a pinned image is the
+        // caller's own, counted when it was pinned)
+        const uint64_t pin = r->dimg ? 0 : std::min<uint64_t>(req_bytes(r), kStagingCap);
         const uint64_t hbm = req_bytes(r) + 12 * r->set->n_chunks;
         if (sv->pinned_used + pin > sv->pinned_budget || sv->hbm_used + hbm > sv->hbm_budget) {
             ++it;
@@ -512,12 +520,27 @@ cudaError_t launch_round(snap_server_s *sv, Round &rd)
         } else if (w.op == OP_GATHER_DIRTY) {
             j.tile_list = r->set->d_dlist + w.c0;
             j.n_tiles = w.c1 - w.c0;
-            j.host = sv->pool_dev + (uint64_t)w.slot * sv->slot_bytes;
+            if (r->dimg) {
+                // straight into the patch: dirty rank c0 + tile, at the slot
+                // the patch layout gave it
+                j.layout = LAYOUT_IMAGE;
+                j.host = r->dimg;
+                j.window_off = w.c0;
+                j.patch_data = r->set->d_patch_data;
+                j.dstart = r->set->d_dstart;
+            } else {
+                j.host = sv->pool_dev + (uint64_t)w.slot * sv->slot_bytes;
+            }
         } else {
             j.tile_begin = w.c0;
             j.n_tiles = w.c1 - w.c0;
-            j.host = sv->pool_dev + (uint64_t)w.slot * sv->slot_bytes;
-            j.window_off = w.b0;
+            if (r->dimg) {
+                j.layout = LAYOUT_IMAGE;
+                j.host = r->dimg;
+            } else {
+                j.host = sv->pool_dev + (uint64_t)w.slot * sv->slot_bytes;
+                j.window_off = w.b0;
+            }
             if (w.op == OP_GATHER) j.hash_out = r->set->d_hash[r->cur];
         }
         rd.h_jobs[q] = j;
@@ -549,7 +572,7 @@ void complete_round(snap_server_s *sv, Round &rd)
         SReq *r = p.first;
         SWin &w = r->wins[p.second];
         if (kerr) fail(sv, r, SNAP_ECUDA);
-        if (w.op == OP_GATHER || w.op == OP_GATHER_DIRTY) {
+        if ((w.op == OP_GATHER || w.op == OP_GATHER_DIRTY) && !r->dimg) {
             if (r->failed) {
                 w.state = W_DONE;
                 sv->free_slots.push_back(w.slot);
@@ -811,6 +834,12 @@ int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, u
     r->image = static_cast<uint8_t *>(image);
     r->cap = cap;
     r->t_arrive = t;
+    // a pinned, mapped image (snap_host_alloc / snap_host_register) over its
+    // whole capacity is used directly
+    if (cap) {
+        uint8_t *d0 = mapped_device_ptr(image), *d1 = mapped_device_ptr(r->image + cap - 1);
+        if (d0 && d1 == d0 + (cap - 1)) r->dimg = d0;
+    }
     // size the request against the tenant's layout (built here when the
     // tenant is idle; a busy tenant's layout cannot change under it)
     if (!tenant->busy.exchange(true)) {

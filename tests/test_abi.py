@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every entry
 point include/snap.h declares (no GPU needed; no compute calls)."""
+import ctypes
 import os
 import re
 import subprocess
@@ -64,10 +65,15 @@ def test_no_gpu_means_a_loud_error_not_a_fallback():
 
 
 def test_host_only_calls_work_without_a_gpu():
-    """The host-side entry points (status names, the two-phase protocol)
-    need no device."""
+    """The host-side entry points (status names, the two-phase protocol,
+    argument checks) need no device."""
     assert snap.strerror(snap.EPEER) != "unknown status"
     seen = []
     rc = snap.coordinate(lambda ph, st: st, lock=lambda: seen.append("l") or 0,
                          run=lambda: seen.append("r") or 0, commit=lambda: seen.append("c"))
     assert rc == snap.OK and seen == ["l", "r", "c"]
+    # argument checks come before any device call
+    buf = (ctypes.c_uint8 * 16)()
+    assert snap.lib().snap_host_register(None, 4096) == snap.EINVAL
+    assert snap.lib().snap_host_register(ctypes.cast(buf, ctypes.c_void_p), 0) == snap.EINVAL
+    assert snap.lib().snap_host_unregister(None) == snap.EINVAL

@@ -59,13 +59,24 @@ def mutate(ts, seed):
     torch.cuda.synchronize()
 
 
-def scenario(mixed: bool):
+PINNED = (0, 3, 4)  # tenants whose images are pinned (direct windows) when pinned=True
+
+
+def scenario(mixed: bool, pinned: bool = False):
     """Phase 1: full checkpoints of 6 tenants; phase 2: incremental (t0, t1),
-    full (t2, t3), restore of the phase-1 image after scribbling (t4, t5)."""
+    full (t2, t3), restore of the phase-1 image after scribbling (t4, t5).
+    With `pinned`, the images of tenants PINNED are registered, so the server
+    reads and writes them directly, and the others stay pageable (staged)."""
     tenants = make_tenants(6, seed=500)
     sv = snap.Server(pinned_budget=64 * MiB, hbm_budget=1 << 40, chunk_bytes=C)
     imgs = [np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8) for s, _ in tenants]
     patches = [np.full(s.image_bytes(snap.INCREMENTAL), 0x5A, dtype=np.uint8) for s, _ in tenants]
+    registered = []
+    if pinned:
+        for t in PINNED:
+            for a in (imgs[t], patches[t]):
+                snap.host_register(a)
+                registered.append(a)
     out = {"phase1_state": [host(ts) for _, ts in tenants]}
 
     def run(reqs):
@@ -87,6 +98,10 @@ def scenario(mixed: bool):
             d.fill_(0x33)
     out["phase2_state"] = [host(ts) for _, ts in tenants]
     full2 = [np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8) for s, _ in tenants]
+    if pinned:
+        for t in PINNED:
+            snap.host_register(full2[t])
+            registered.append(full2[t])
     reqs = [(tenants[0][0], snap.REQ_INCREMENTAL, patches[0]), (tenants[1][0], snap.REQ_INCREMENTAL, patches[1]),
             (tenants[2][0], snap.REQ_FULL, full2[2]), (tenants[3][0], snap.REQ_FULL, full2[3]),
             (tenants[4][0], snap.REQ_RESTORE, imgs[4]), (tenants[5][0], snap.REQ_RESTORE, imgs[5])]
@@ -97,12 +112,15 @@ def scenario(mixed: bool):
     out["restored"] = [host(tenants[t][1]) for t in (4, 5)]
     out["latency_ms"] = [st["total_ms"] for st in stats1 + stats2]
     sv.close()
+    for a in registered:
+        snap.host_unregister(a)
     return out
 
 
-def test_serving_mix_equals_alone_equals_oracle():
-    mixed = scenario(mixed=True)
-    alone = scenario(mixed=False)
+@pytest.mark.parametrize("pinned", [False, True])
+def test_serving_mix_equals_alone_equals_oracle(pinned):
+    mixed = scenario(mixed=True, pinned=pinned)
+    alone = scenario(mixed=False, pinned=pinned)
     for key in ("full1", "incr", "full2"):
         for a, b in zip(mixed[key], alone[key]):
             assert np.array_equal(a, b), key
