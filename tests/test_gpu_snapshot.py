@@ -296,6 +296,41 @@ def test_ring_pageable_images(C, ring):
     assert s.committed_hashes(sum(nch))[1] == 0
 
 
+def test_registered_numpy_image_is_used_directly():
+    """A caller's numpy buffer pinned with host_register is an image like
+    snap_host_alloc memory: the full image equals the oracle's, an
+    incremental patch too, and the restore from it brings every byte back;
+    unregistering twice is EINVAL."""
+    C = 65536
+    sizes = [3 * C + 100, C, 0, 5000, 2 * C]
+    ts, hs = device_state(sizes, seed=61)
+    s = make_set(ts, C)
+    full = np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8)
+    patch = np.full(s.image_bytes(snap.INCREMENTAL), 0x5A, dtype=np.uint8)
+    snap.host_register(full)
+    snap.host_register(patch)
+    try:
+        used = s.checkpoint(full, snap.FULL)
+        assert np.array_equal(full[:used], oracle.write_full(hs, C, 0)[1])
+        mutate(ts, C, [(0, 1), (4, 1)])
+        cur = readback(ts)
+        used_p = s.checkpoint(patch, snap.INCREMENTAL)
+        exp = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in hs], 1, 0)[1]
+        assert used_p == exp.size and np.array_equal(patch[:used_p], exp)
+        for d in ts:
+            d.zero_()
+        s.restore(full, used)
+        for a, b in zip(readback(ts), hs):
+            assert np.array_equal(a, b)
+    finally:
+        snap.host_unregister(full)
+        snap.host_unregister(patch)
+    with pytest.raises(snap.SnapError) as e:
+        snap.host_unregister(full)
+    assert e.value.status == snap.EINVAL
+    s.close()
+
+
 def test_ring_pageable_windows_smaller_than_slots():
     """A 640 MiB state through a 4 GiB ring: windows of about 20 MiB (1/32
     of the state) in 256 MiB slots, 32 or more of them, so the 16 slots are
