@@ -40,6 +40,7 @@ namespace {
 
 constexpr int kRounds = 2;
 constexpr size_t kMinBatch = 8;  // windows a round waits for while another runs
+constexpr int kRoundWindowsPerRequest = 8;  // 512 MiB of 64 MiB windows
 constexpr uint64_t kStagingCap = 2ull << 30;  // pinned staging charged per request
 
 static inline uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
@@ -475,12 +476,18 @@ size_t count_ready(const snap_server_s *sv)
 bool build_round(snap_server_s *sv, Round &rd)
 {
     rd.wins.clear();
+    // at most kRoundWindowsPerRequest windows of one request per round: a
+    // request whose windows are all ready at once (a pinned image) would
+    // otherwise fill a round alone, one link direction for its whole length
+    std::vector<int> taken(sv->active.size(), 0);
     bool progress = true;
     while ((int)rd.wins.size() < kMaxJobs && progress) {
         progress = false;
-        for (SReq *r : sv->active) {
+        for (size_t a = 0; a < sv->active.size(); ++a) {
+            SReq *r = sv->active[a];
             if ((int)rd.wins.size() >= kMaxJobs) break;
             if (r->phase != P_WINDOWS && r->phase != P_HASH) continue;
+            if (taken[a] >= kRoundWindowsPerRequest) continue;
             for (size_t i = 0; i < r->wins.size(); ++i) {
                 SWin &w = r->wins[i];
                 bool take = false;
@@ -493,6 +500,7 @@ bool build_round(snap_server_s *sv, Round &rd)
                 if (take) {
                     w.state = W_LAUNCHED;
                     rd.wins.emplace_back(r, i);
+                    ++taken[a];
                     progress = true;
                     break;  // one window per request per pass: fair interleaving
                 }
