@@ -2,13 +2,15 @@
 // tenant sets, continuously batched into shared persistent launches.
 //
 // A scheduler thread owns the GPU side.  Requests wait in arrival order and
-// are admitted while the pinned-host and HBM budgets allow (a request
-// charges min(its bytes, 2 GiB) of pinned staging and its tenant's resident
-// state plus scratch of HBM).  Each admitted request is cut into windows of
-// chunk tiles; every round the scheduler packs up to 64 windows from all
-// admitted requests -- round-robin in arrival order -- into ONE launch of
-// the persistent tile kernel (one job per window), so tiles of requests that
-// arrived at different times share the GPU.  Two rounds are kept in flight.
+// are admitted while the pinned-host and HBM budgets allow (a request with a
+// pageable image charges min(its bytes, 2 GiB) of pinned staging; every
+// request charges its tenant's resident state plus scratch of HBM).  Each
+// admitted request is cut into windows of chunk tiles; every round the
+// scheduler packs up to 64 windows from all admitted requests -- one window
+// per request per pass, shortest remaining work first, at most 8 of one
+// request -- into ONE launch of the persistent tile kernel (one job per
+// window), so tiles of requests that arrived at different times share the
+// GPU.  Two rounds are kept in flight.
 // Host workers move window data between the server's pinned slots and the
 // tenants' pageable images: slots are filled before a restore window
 // launches and drained after a checkpoint window completes.  A pinned,
