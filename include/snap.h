@@ -145,9 +145,11 @@ SNAP_API int snap_set_prepare(snap_set s, int what);
 SNAP_API int snap_image_bytes(snap_set s, int mode, uint64_t *out);
 
 /* Pinned, device-mapped host memory for images (cudaHostAlloc, mapped and
- * portable).  Images in such memory are written/read by the kernels directly
- * over the host link; any other (pageable) image goes through the set's
- * pinned ring.  Free with snap_host_free.  Errors: EINVAL, ENOMEM. */
+ * portable).  An image whose bytes all lie in one such region (or one
+ * snap_host_register region) is written/read by the kernels directly over
+ * the host link; any other image -- pageable, pinned by other means, or only
+ * partly inside a region -- goes through the set's pinned ring.  Free with
+ * snap_host_free.  Errors: EINVAL, ENOMEM. */
 SNAP_API int snap_host_alloc(uint64_t bytes, void **out);
 SNAP_API int snap_host_free(void *p);
 
@@ -311,8 +313,9 @@ SNAP_API int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_b
  * first call on each device looks up that array (cudaGetSymbolAddress):
  * make it before any stream capture.  Calls share the array: two calls
  * whose GPU work overlaps (other streams or threads on the same device)
- * race; this process's host calls are serialised.  Runs on `stream` and
- * waits for it. */
+ * race; this process's host calls are serialised.  Every call copies its
+ * descriptor block from host memory onto `stream`, runs there, and
+ * synchronises `stream` before it returns. */
 #define SNAP_NOALLOC_MAX_BUFFERS 1024u
 SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *bytes, uint32_t n_buffers,
                                       uint64_t chunk_bytes, uint32_t *hashes, void *stream);

@@ -105,7 +105,7 @@ int snap_checkpoint_async(snap_set s, void *host_image, uint64_t cap, int mode)
     if (mode == SNAP_INCREMENTAL && !s->has_base) return SNAP_ENOBASE;
     if (mode == SNAP_FULL && cap < s->full_bytes) return SNAP_EINVAL;
     if (mode == SNAP_INCREMENTAL && cap < SNAP_IMG_HEADER_BYTES) return SNAP_EINVAL;
-    uint8_t *dimg = mapped_device_ptr(host_image);
+    uint8_t *dimg = mapped_image_ptr(host_image, image_extent(s, mode, cap));
     if (!dimg) return SNAP_EINVAL;  // the background part writes through the mapping
     rc = async_prepare(s);
     if (rc) return rc;

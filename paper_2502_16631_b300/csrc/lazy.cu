@@ -124,7 +124,7 @@ int snap_restore_async(const void *host_image, uint64_t bytes, snap_set s, const
     if (h.flags & SNAP_IMG_FLAG_INCREMENTAL) return SNAP_EFORMAT;  // merge patches first
     rc = walk_records(s, img, bytes, h, s->h_hash_stage);
     if (rc) return rc;
-    uint8_t *dimg = mapped_device_ptr(host_image);
+    uint8_t *dimg = mapped_image_ptr(host_image, bytes);
     if (!dimg) return SNAP_EINVAL;  // the waves read through the mapping
     rc = lazy_prepare(s);
     if (rc) return rc;

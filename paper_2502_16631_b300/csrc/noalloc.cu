@@ -23,7 +23,9 @@
 //    order.
 //  - the first call on each device looks up the array's device address
 //    (cudaGetSymbolAddress) and opts the kernel into its shared memory; make
-//    that first call before any stream capture.
+//    that first call before any stream capture;
+//  - every call copies its descriptor block to the device from a static
+//    host block and synchronises the caller's stream before it returns.
 #include "snap.h"
 #include "runtime_internal.h"
 

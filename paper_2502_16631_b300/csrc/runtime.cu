@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <thread>
 
@@ -70,6 +71,52 @@ uint8_t *mapped_device_ptr(const void *host)
     }
     if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
     return static_cast<uint8_t *>(at.devicePointer);
+}
+
+// The host regions this library pinned and mapped for images
+// (snap_host_alloc, snap_host_register): base -> bytes.  A caller's image is
+// read or written by the kernels through its mapping only when the whole
+// range the kernels touch lies inside one such region; a mapping of the
+// first byte alone says nothing about the rest (a partly registered buffer,
+// or two registrations with an unmapped gap between them).
+namespace {
+std::mutex g_pinned_mu;
+std::map<uintptr_t, uint64_t> g_pinned;
+}  // namespace
+
+void pinned_add(const void *p, uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned[(uintptr_t)p] = bytes;
+}
+
+void pinned_remove(const void *p)
+{
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned.erase((uintptr_t)p);
+}
+
+bool pinned_covers(const void *p, uint64_t len)
+{
+    const uintptr_t a = (uintptr_t)p;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned.upper_bound(a);
+    if (it == g_pinned.begin()) return false;
+    --it;
+    const uintptr_t lo = it->first;
+    const uint64_t n = it->second;
+    return a >= lo && a - lo <= n && len <= n - (a - lo);
+}
+
+uint8_t *mapped_image_ptr(const void *host, uint64_t len)
+{
+    if (!host || !pinned_covers(host, len)) return nullptr;
+    return mapped_device_ptr(host);
+}
+
+uint64_t image_extent(const snap_set_s *s, int mode, uint64_t cap)
+{
+    return mode == SNAP_FULL ? s->full_bytes : std::min(cap, s->patch_bound);
 }
 
 void write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n, uint64_t total, uint64_t gen,
@@ -782,12 +829,14 @@ int snap_host_alloc(uint64_t bytes, void **out)
         *out = nullptr;
         return SNAP_ENOMEM;
     }
+    pinned_add(*out, bytes);
     return SNAP_OK;
 }
 
 int snap_host_free(void *p)
 {
     if (!p) return SNAP_OK;
+    pinned_remove(p);
     return cuda_status(cudaFreeHost(p));
 }
 
@@ -795,7 +844,10 @@ int snap_host_register(void *p, uint64_t bytes)
 {
     if (!p || bytes == 0) return SNAP_EINVAL;
     const cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterMapped | cudaHostRegisterPortable);
-    if (e == cudaSuccess) return SNAP_OK;
+    if (e == cudaSuccess) {
+        pinned_add(p, bytes);
+        return SNAP_OK;
+    }
     cudaGetLastError();
     if (e == cudaErrorHostMemoryAlreadyRegistered || e == cudaErrorInvalidValue) return SNAP_EINVAL;
     return e == cudaErrorMemoryAllocation ? SNAP_ENOMEM : SNAP_ECUDA;
@@ -805,7 +857,10 @@ int snap_host_unregister(void *p)
 {
     if (!p) return SNAP_EINVAL;
     const cudaError_t e = cudaHostUnregister(p);
-    if (e == cudaSuccess) return SNAP_OK;
+    if (e == cudaSuccess) {
+        pinned_remove(p);
+        return SNAP_OK;
+    }
     cudaGetLastError();
     return e == cudaErrorHostMemoryNotRegistered || e == cudaErrorInvalidValue ? SNAP_EINVAL : SNAP_ECUDA;
 }
@@ -946,7 +1001,7 @@ int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64
     if (mode == SNAP_FULL && cap < s->full_bytes) return SNAP_EINVAL;
     if (mode == SNAP_INCREMENTAL && cap < SNAP_IMG_HEADER_BYTES) return SNAP_EINVAL;
 
-    uint8_t *dimg = mapped_device_ptr(host_image);
+    uint8_t *dimg = mapped_image_ptr(host_image, image_extent(s, mode, cap));
     rc = quiesce(s, deadline);
     if (rc) return rc;
     const double tq = now_ms();
@@ -1010,7 +1065,7 @@ static int coord_lock(void *p)
     if (c.mode == SNAP_INCREMENTAL && !s->has_base) return SNAP_ENOBASE;
     if (c.mode == SNAP_FULL && c.cap < s->full_bytes) return SNAP_EINVAL;
     if (c.mode == SNAP_INCREMENTAL && c.cap < SNAP_IMG_HEADER_BYTES) return SNAP_EINVAL;
-    c.dimg = mapped_device_ptr(c.image);
+    c.dimg = mapped_image_ptr(c.image, image_extent(s, c.mode, c.cap));
     rc = quiesce(s, c.deadline);
     c.tq = now_ms();
     return rc;
@@ -1106,7 +1161,7 @@ static int restore_lock(snap_set_s *s, const uint8_t *img, uint64_t bytes, Image
 static int restore_run(snap_set_s *s, const uint8_t *img, uint64_t bytes, const ImageHeader &h, double t0, double tq,
                        double deadline)
 {
-    uint8_t *dimg = mapped_device_ptr(img);
+    uint8_t *dimg = mapped_image_ptr(img, bytes);
     if (!dimg) {
         ImageIO io;
         io.mem = const_cast<uint8_t *>(img);  // read only: restore copies image -> ring

@@ -147,6 +147,17 @@ bool fault_injected(const char *what);
 int cuda_status(cudaError_t e);
 int wait_event(cudaEvent_t ev, double deadline_ms);
 uint8_t *mapped_device_ptr(const void *host);
+// Pinned image regions (snap_host_alloc / snap_host_register): the mapped
+// device address of [host, host+len) if that whole range lies inside one
+// recorded region, else nullptr (the caller then stages through the ring,
+// or refuses where only a mapping will do).
+void pinned_add(const void *p, uint64_t bytes);
+void pinned_remove(const void *p);
+bool pinned_covers(const void *p, uint64_t len);
+uint8_t *mapped_image_ptr(const void *host, uint64_t len);
+// Bytes of the caller's image a checkpoint's kernels may touch: the full
+// image, or for a patch the smaller of its capacity and the largest patch.
+uint64_t image_extent(const snap_set_s *s, int mode, uint64_t cap);
 void write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n, uint64_t total, uint64_t gen, uint64_t parent);
 int parse_header(const uint8_t *img, uint64_t len, ImageHeader *h);
 int walk_records(const snap_set_s *s, const uint8_t *img, uint64_t len, const ImageHeader &h, uint32_t *hashes);

@@ -42,7 +42,7 @@ namespace {
 
 constexpr int kRounds = 2;
 constexpr size_t kMinBatch = 8;  // windows a round waits for while another runs
-constexpr int kRoundWindowsPerRequest = 8;  // 512 MiB of 64 MiB windows
+constexpr int kRoundWindowsPerRequest = 8;  // windows of one request per round (each at most one slot)
 constexpr uint64_t kStagingCap = 2ull << 30;  // pinned staging charged per request
 
 static inline uint64_t upg(uint64_t x) { return (x + 4095u) & ~uint64_t(4095u); }
@@ -844,12 +844,9 @@ int snap_server_submit(snap_server sv, snap_set tenant, int kind, void *image, u
     r->image = static_cast<uint8_t *>(image);
     r->cap = cap;
     r->t_arrive = t;
-    // a pinned, mapped image (snap_host_alloc / snap_host_register) over its
-    // whole capacity is used directly
-    if (cap) {
-        uint8_t *d0 = mapped_device_ptr(image), *d1 = mapped_device_ptr(r->image + cap - 1);
-        if (d0 && d1 == d0 + (cap - 1)) r->dimg = d0;
-    }
+    // an image whose whole capacity lies in one pinned, mapped region
+    // (snap_host_alloc / snap_host_register) is used directly
+    if (cap) r->dimg = mapped_image_ptr(image, cap);
     // size the request against the tenant's layout (built here when the
     // tenant is idle; a busy tenant's layout cannot change under it)
     if (!tenant->busy.exchange(true)) {

@@ -126,7 +126,7 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
     uint8_t *dimg = nullptr;
     if (mode == SNAP_FULL) {
         if (!host_image || cap < need) return SNAP_EINVAL;
-        dimg = mapped_device_ptr(host_image);
+        dimg = mapped_image_ptr(host_image, need);
         if (!dimg) return SNAP_EINVAL;
     }
     if (s->n_chunks == 0) return SNAP_EINVAL;

@@ -328,6 +328,56 @@ def test_registered_numpy_image_is_used_directly():
     with pytest.raises(snap.SnapError) as e:
         snap.host_unregister(full)
     assert e.value.status == snap.EINVAL
+
+
+def test_partly_registered_image_is_staged_not_mapped():
+    """An image buffer of which only a part is pinned (or which two separate
+    registrations cover) is not read or written through its mapping: the
+    synchronous calls stage it through the ring and still match the oracle,
+    and the calls that need a mapping over the whole image (asynchronous
+    checkpoint, prioritised restore) refuse it with EINVAL."""
+    C = 65536
+    sizes = [5 * C + 100, 2 * C, 0, 7000, 3 * C]
+    ts, hs = device_state(sizes, seed=67)
+    s = make_set(ts, C, ring_bytes=1 << 20)
+    n = s.image_bytes(snap.FULL)
+    import mmap
+    m = mmap.mmap(-1, n + 8192)  # page-aligned, so the two halves share no page
+    full = np.frombuffer(m, dtype=np.uint8)
+    full[:] = 0xA5
+    half = (n // 2) & ~4095
+    lo, hi = full[:half], full[half:]
+    snap.host_register(lo)
+    try:
+        exp = oracle.write_full(hs, C, 0)[1]
+        used = s.checkpoint(full, snap.FULL)
+        assert np.array_equal(full[:used], exp)
+        assert s.checkpoint_async_status(full, snap.FULL) == snap.EINVAL
+        assert s.restore_async_status(full, (), used) == snap.EINVAL
+        for d in ts:
+            d.zero_()
+        s.restore(full, used)
+        for a, b in zip(readback(ts), hs):
+            assert np.array_equal(a, b)
+        # two registrations side by side still leave the image in two regions
+        snap.host_register(hi)
+        try:
+            full[:used] = 0
+            used = s.checkpoint(full, snap.FULL)
+            assert np.array_equal(full[:used], exp)
+            assert s.checkpoint_async_status(full, snap.FULL) == snap.EINVAL
+            for d in ts:
+                d.zero_()
+            s.restore(full, used)
+            for a, b in zip(readback(ts), hs):
+                assert np.array_equal(a, b)
+        finally:
+            snap.host_unregister(hi)
+    finally:
+        snap.host_unregister(lo)
+    s.close()
+    del lo, hi, full
+    m.close()
     s.close()
 
 

@@ -6,13 +6,16 @@ untouched, a process whose pool is exhausted or owned by another framework).
 It must give exactly the hashes snap_hash_chunks gives buffer by buffer --
 hashes are integers, so the comparison is exact -- on two calls in a row,
 the second with a different buffer list, so that nothing left in the shared
-static scratch by the first call leaks into the second.  This file is
-collected last; it passes alone in a fresh process and after the others."""
+static scratch by the first call leaks into the second.  Both are also held
+to the CPU oracle's CRC-32C of the same bytes (read back with a plain
+device-to-host copy).  This file is collected last; it passes alone in a
+fresh process and after the others."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 import paper_2502_16631_b300 as snap
 
 pytestmark = [pytest.mark.gpu,
@@ -41,6 +44,13 @@ def noalloc(buffers, C):
     return out[:total].cpu().numpy().view(np.uint32)
 
 
+def expected(buffers, C):
+    """The oracle's chunk hashes of the buffers' bytes, in call order."""
+    torch.cuda.synchronize()
+    out = [oracle.chunk_hashes(t.cpu().numpy(), C) for t in buffers if t.numel()]
+    return np.concatenate(out) if out else np.zeros(0, np.uint32)
+
+
 def buffers_of(sizes, seed):
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
@@ -52,13 +62,17 @@ def test_noalloc_matches_allocating_hasher_twice(C):
     first = buffers_of([3 * C + 100, 1, 0, C, 12345, 5 * C], seed=1)
     second = buffers_of([C - 16, 2 * C + 1], seed=2)  # fewer buffers than the first call
     for bufs in (first, second):
-        assert np.array_equal(noalloc(bufs, C), reference(bufs, C))
+        got = noalloc(bufs, C)
+        assert np.array_equal(got, reference(bufs, C))
+        assert np.array_equal(got, expected(bufs, C))
 
 
 def test_noalloc_many_buffers_and_limit():
     C = 4096
     bufs = buffers_of([4096 + 16 * k for k in range(snap.NOALLOC_MAX_BUFFERS)], seed=3)
-    assert np.array_equal(noalloc(bufs, C), reference(bufs, C))
+    got = noalloc(bufs, C)
+    assert np.array_equal(got, reference(bufs, C))
+    assert np.array_equal(got, expected(bufs, C))
     # one buffer over the static scratch's capacity is refused, nothing launched
     over = bufs + bufs[:1]
     out = torch.zeros(4, dtype=torch.int32, device="cuda")
