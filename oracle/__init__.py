@@ -60,6 +60,7 @@ def lib():
         L.orc_image_bytes.restype = u64
         L.orc_image_bytes.argtypes = [u64, u64p, u64]
         L.orc_write_full.argtypes = [u64, pp, u64p, u64, u64, u8p, u64, u64p]
+        L.orc_write_full_window.argtypes = [u64, pp, u64p, u64, u64, u64, u64, u8p, u64, u64p, u64p]
         L.orc_read_header.argtypes = [u8p, u64, u64p]
         L.orc_restore.argtypes = [u8p, u64, u64, pp, u64p]
         L.orc_verify.argtypes = [u8p, u64, u64, pp, u64p, u64p]
@@ -129,6 +130,26 @@ def write_full(datas, chunk: int, generation: int = 0, out: np.ndarray | None = 
     rc = lib().orc_write_full(len(arrs), ptrs, sizes, chunk, generation, _ptr(out), out.size,
                               ctypes.byref(used))
     return rc, out[: used.value]
+
+
+def write_full_window(sizes, datas, chunk: int, generation: int, k0: int, k1: int):
+    """Bytes [lo, hi) of the full image of allocations of `sizes`: from the
+    header (k0 == 0) or record k0 to the end of record k1 - 1; `datas` holds
+    the bytes of allocations k0..k1-1 only.  Returns (status, lo, array)."""
+    n = len(sizes)
+    arrs = [np.ascontiguousarray(d, dtype=np.uint8).reshape(-1) for d in datas]
+    assert len(arrs) == k1 - k0
+    ptrs = (ctypes.c_void_p * max(1, n))()
+    for j, a in enumerate(arrs):
+        assert a.size == sizes[k0 + j]
+        ptrs[k0 + j] = _ptr(a) if a.size else None
+    sz = (ctypes.c_uint64 * max(1, n))(*sizes)
+    lo_b = image_bytes(list(sizes[:k0]), chunk) if k0 else 0
+    out = np.empty(max(1, image_bytes(list(sizes[:k1]), chunk) - lo_b), dtype=np.uint8)
+    lo, used = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    rc = lib().orc_write_full_window(n, ptrs, sz, chunk, generation, k0, k1, _ptr(out), out.size,
+                                     ctypes.byref(lo), ctypes.byref(used))
+    return rc, int(lo.value), out[: used.value]
 
 
 def read_header(img: np.ndarray):

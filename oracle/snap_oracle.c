@@ -192,23 +192,32 @@ static void orc_write_header(uint8_t *h, uint32_t flags, uint64_t C, uint64_t n,
     orc_put32(h + 56, orc_crc32c(h, 56));
 }
 
-/* Write the full image of n allocations into out[0..cap). */
-int orc_write_full(uint64_t n, const uint8_t *const *data, const uint64_t *sizes,
-                   uint64_t C, uint64_t generation, uint8_t *out, uint64_t cap,
-                   uint64_t *used)
+/* Write the bytes [lo, hi) of the full image of n allocations into
+ * out[0..cap): lo = 0 when k0 == 0 (the header is included), else the
+ * offset of record k0; hi = the end of record k1 - 1 (the header's end when
+ * k1 == 0).  Those are exactly the bytes the whole image holds there; only
+ * data[k0..k1) is read (data[k] for k outside may be NULL), so an image too
+ * large for memory can be produced and compared record by record.
+ * *lo_out = lo, *used = hi - lo. */
+int orc_write_full_window(uint64_t n, const uint8_t *const *data, const uint64_t *sizes,
+                          uint64_t C, uint64_t generation, uint64_t k0, uint64_t k1,
+                          uint8_t *out, uint64_t cap, uint64_t *lo_out, uint64_t *used)
 {
-    if (!orc_valid_chunk(C)) return ORC_EINVAL;
-    uint64_t need = orc_image_bytes(n, sizes, C);
-    if (cap < need) return ORC_EINVAL;
-    uint64_t total = 0;
-    for (uint64_t k = 0; k < n; ++k) total += sizes[k];
-    memset(out, 0, need);
-    orc_write_header(out, ORC_FLAG_DEV, C, n, total, generation, 0);
-    uint64_t off = ORC_HDR;
-    for (uint64_t k = 0; k < n; ++k) {
+    if (!orc_valid_chunk(C) || k0 > k1 || k1 > n) return ORC_EINVAL;
+    uint64_t lo = k0 ? orc_image_bytes(k0, sizes, C) : 0;
+    uint64_t hi = orc_image_bytes(k1, sizes, C);
+    if (cap < hi - lo) return ORC_EINVAL;
+    memset(out, 0, hi - lo);
+    if (k0 == 0) {
+        uint64_t total = 0;
+        for (uint64_t k = 0; k < n; ++k) total += sizes[k];
+        orc_write_header(out, ORC_FLAG_DEV, C, n, total, generation, 0);
+    }
+    uint64_t off = k0 ? lo : ORC_HDR;   /* image offset of record k */
+    for (uint64_t k = k0; k < k1; ++k) {
         uint64_t nk = orc_n_chunks(sizes[k], C);
         uint64_t data_off = orc_up(off + ORC_REC + 4 * nk);
-        uint8_t *rec = out + off;
+        uint8_t *rec = out + (off - lo);
         orc_put64(rec, sizes[k]);
         orc_put64(rec + 8, nk);
         orc_put64(rec + 16, data_off);
@@ -219,11 +228,22 @@ int orc_write_full(uint64_t n, const uint8_t *const *data, const uint64_t *sizes
         orc_chunk_hashes(data[k], sizes[k], C, h);
         for (uint64_t i = 0; i < nk; ++i) orc_put32(rec + ORC_REC + 4 * i, h[i]);
         free(h);
-        memcpy(out + data_off, data[k], sizes[k]);
+        memcpy(out + (data_off - lo), data[k], sizes[k]);
         off = orc_up(data_off + sizes[k]);
     }
-    *used = need;
+    *lo_out = lo;
+    *used = hi - lo;
     return ORC_OK;
+}
+
+/* Write the full image of n allocations into out[0..cap): the window of
+ * every record. */
+int orc_write_full(uint64_t n, const uint8_t *const *data, const uint64_t *sizes,
+                   uint64_t C, uint64_t generation, uint8_t *out, uint64_t cap,
+                   uint64_t *used)
+{
+    uint64_t lo = 0;
+    return orc_write_full_window(n, data, sizes, C, generation, 0, n, out, cap, &lo, used);
 }
 
 /* Parsed view of an image (full or patch). */

@@ -36,7 +36,8 @@ struct Ring {
     uint8_t *dev = nullptr;   // its device-visible address
     uint64_t bytes = 0, slot_bytes = 0;
     int slots = 0;
-    std::vector<cudaEvent_t> ev;  // one per slot: the last kernel that used it
+    std::vector<cudaEvent_t> ev;   // one per slot: the end of the last kernel that used it
+    std::vector<cudaEvent_t> ev0;  // one per slot: the start of that kernel (device timing)
     Pool *pool = nullptr;
     Job *d_jobs = nullptr;   // one job per slot (device)
     Job *h_jobs = nullptr;   // pinned staging
@@ -49,7 +50,8 @@ void ring_free(snap_set_s *s)
     if (!r) return;
     if (s->st) cudaStreamSynchronize(s->st);
     delete r->pool;
-    for (auto e : r->ev) cudaEventDestroy(e);
+    for (auto e : r->ev) if (e) cudaEventDestroy(e);
+    for (auto e : r->ev0) if (e) cudaEventDestroy(e);
     cudaFreeHost(r->host);
     cudaFree(r->d_jobs);
     cudaFreeHost(r->h_jobs);
@@ -81,7 +83,9 @@ int ring_get(snap_set_s *s, Ring **out)
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&r->h_jobs, sizeof(Job) * slots, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_cursor, sizeof(unsigned long long) * slots);
     r->ev.assign(slots, nullptr);
-    for (int i = 0; i < slots && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&r->ev[i], cudaEventDisableTiming);
+    r->ev0.assign(slots, nullptr);
+    for (int i = 0; i < slots && e == cudaSuccess; ++i) e = cudaEventCreate(&r->ev[i]);
+    for (int i = 0; i < slots && e == cudaSuccess; ++i) e = cudaEventCreate(&r->ev0[i]);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->ring = r;
@@ -219,16 +223,38 @@ static Job window_job(const snap_set_s *s, Ring *r, int slot, uint32_t op, const
     return j;
 }
 
-// Launch one window's tile kernel into its slot and record the slot event.
+// Launch one window's tile kernel into its slot between the slot's two
+// events (start, end).
 static cudaError_t launch_window(snap_set_s *s, Ring *r, int slot, const Job &j, const TileShape &sh,
                                  const CombineConsts &cc)
 {
     r->h_jobs[slot] = j;
     cudaError_t e = cudaMemcpyAsync(r->d_jobs + slot, r->h_jobs + slot, sizeof(Job), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_cursor + slot, 0, sizeof(unsigned long long), s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev0[slot], s->st);
     if (e == cudaSuccess) e = launch_tiles(r->d_jobs + slot, 1, r->d_cursor + slot, cc, sh, &s->d_cb->res, s->st);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev[slot], s->st);
     return e;
+}
+
+// Device time (ms) of the kernel last launched into `slot`, once its end
+// event has completed; the sum over a call's windows is its copy_ms.
+static double slot_kernel_ms(Ring *r, int slot)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r->ev0[slot], r->ev[slot]) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return ms;
+}
+
+// The kernels of the last min(W, slots) windows, after the stream is drained.
+static double tail_kernel_ms(Ring *r, size_t W)
+{
+    double ms = 0.0;
+    for (size_t w = W > (size_t)r->slots ? W - r->slots : 0; w < W; ++w) ms += slot_kernel_ms(r, (int)(w % r->slots));
+    return ms;
 }
 
 uint64_t parts_for(uint64_t bytes, int threads)
@@ -277,7 +303,7 @@ static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double d
     const TileShape sh = s->shape[SHAPE_GATHER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
     int rc = SNAP_OK;
-    const double tk0 = now_ms();
+    double kms = 0.0;
     for (size_t w = 0; w < W && e == cudaSuccess && rc == SNAP_OK; ++w) {
         const int slot = (int)(w % r->slots);
         if (w >= (size_t)r->slots) {
@@ -285,6 +311,7 @@ static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double d
             if (!pg.wait(deadline, [&] { return pg.left[prev] == 0; })) rc = SNAP_ETIMEDOUT;
             if (pg.err) rc = pg.err;
             if (rc) break;
+            kms += slot_kernel_ms(r, slot);  // its copy-out waited for the kernel
         }
         e = launch_window(s, r, slot, window_job(s, r, slot, OP_GATHER, win[w], s->d_hash[cur]), sh, cc);
         if (e != cudaSuccess) break;
@@ -322,7 +349,7 @@ static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double d
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda_status(e);
     if (s->h_res->err) return SNAP_ECUDA;
-    st.copy_ms = now_ms() - tk0;
+    st.copy_ms = kms + tail_kernel_ms(r, W);
     // metadata: records, hashes and padding (the data regions are written)
     for (size_t k = 0; k < s->desc.size(); ++k) {
         const AllocDesc &a = s->desc[k];
@@ -419,7 +446,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
     pg.left.assign(W, 0);
     const TileShape shg = s->shape[SHAPE_GATHER];
     const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
-    const double tc0 = now_ms();
+    double kms = 0.0;
     int rc = SNAP_OK;
     for (size_t w = 0; w < W && rc == SNAP_OK; ++w) {
         const int slot = (int)(w % r->slots);
@@ -428,6 +455,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
             if (!pg.wait(deadline, [&] { return pg.left[prev] == 0; })) rc = SNAP_ETIMEDOUT;
             if (pg.err) rc = pg.err;
             if (rc) break;
+            kms += slot_kernel_ms(r, slot);
         }
         const uint64_t r0 = w * per, r1 = std::min<uint64_t>(nd, r0 + per);
         Job j{};
@@ -490,7 +518,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda_status(e);
     if (s->h_res->err) return SNAP_ECUDA;
-    st.copy_ms = now_ms() - tc0;
+    st.copy_ms = kms + tail_kernel_ms(r, W);
     *used = s->h_res->patch_bytes;
     st.image_bytes = *used;
     st.dirty_chunks = nd;
@@ -554,7 +582,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
     if (e != cudaSuccess) return cuda_status(e);
     const TileShape sh = s->shape[SHAPE_SCATTER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
-    const double tc0 = now_ms();
+    double kms = 0.0;
 
     // queue the fill of window w: it waits for the kernel of window w - slots
     auto queue_fill = [&](size_t w) {
@@ -589,6 +617,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
         if (!pg.wait(deadline, [&] { return pg.left[w] == 0; })) rc = SNAP_ETIMEDOUT;
         if (pg.err) rc = pg.err;
         if (rc) break;
+        if (w >= (size_t)r->slots) kms += slot_kernel_ms(r, slot);  // its fill waited for that kernel
         e = launch_window(s, r, slot, window_job(s, r, slot, OP_SCATTER, win[w], nullptr), sh, cc);
         if (e != cudaSuccess) {
             rc = cuda_status(e);
@@ -628,7 +657,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
     st.total_chunks = s->n_chunks;
     st.generation = h.generation;
     st.quiesce_ms = tq - t0;
-    st.copy_ms = now_ms() - tc0;
+    st.copy_ms = kms + tail_kernel_ms(r, W);
     st.kernel_launches = W;
     st.total_ms = now_ms() - t0;
     st.frozen_ms = st.total_ms;

@@ -65,6 +65,29 @@ def test_full_image_layout(C, hwcrc):
     assert not img[~covered].any()
 
 
+@pytest.mark.parametrize("C", [4096, 65536])
+def test_full_image_windows(C):
+    """The record-window writer used for states too large to image whole:
+    each window starts at the written layout's offset of its first record
+    (0 when it holds the header), reads only its own allocations, and the
+    windows of any split put end to end are the whole image."""
+    datas = make(SIZES, seed=3)
+    whole = oracle.write_full(datas, C, generation=4)[1]
+    recs, _, total = layout(SIZES, C)
+    n = len(SIZES)
+    for cuts in ([0, n], [0, 1, n], [0, 2, 3, 5, n], list(range(n + 1)), [0, 4, 4, n]):
+        parts = []
+        for k0, k1 in zip(cuts, cuts[1:]):
+            rc, lo, w = oracle.write_full_window(SIZES, datas[k0:k1], C, 4, k0, k1)
+            assert rc == 0
+            assert lo == (0 if k0 == 0 else recs[k0] if k0 < n else total)
+            assert lo + w.size == (recs[k1] if k1 < n else total)
+            parts.append(w)
+        assert np.array_equal(np.concatenate(parts), whole)
+    rc, lo, w = oracle.write_full_window(SIZES, [], C, 4, 0, 0)  # the header alone
+    assert rc == 0 and lo == 0 and np.array_equal(w, whole[:64])
+
+
 def test_image_bytes_closed_form():
     for C in (4096, 16384, 65536, 1 << 20):
         sizes = workloads.config1_sizes(3)
