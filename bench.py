@@ -1086,8 +1086,13 @@ def run_serving(args, rank, world, local, pg):
         full = np.frombuffer(mmap.mmap(-1, nf, flags=flags), dtype=np.uint8)
         patch = np.frombuffer(mmap.mmap(-1, npb, flags=flags), dtype=np.uint8)
         nunits = sum((n + UNIT - 1) // UNIT for n in sizes)
+        rec, o = [], 64  # record offsets of the full image (the image layout)
+        for n in sizes:
+            nk = (n + UNIT - 1) // UNIT
+            rec.append(o)
+            o = ((o + 32 + 4 * nk + 4095) // 4096 * 4096 + n + 4095) // 4096 * 4096
         T.append({"set": s, "ts": ts, "full": full, "patch": patch, "bytes": sum(sizes), "units": nunits,
-                  "has_image": False})
+                  "has_image": False, "sizes": sizes, "rec": rec})
     torch.cuda.synchronize()
     # arrivals
     r = workloads.Rng(args.seed ^ 0xA77)
@@ -1140,6 +1145,47 @@ def run_serving(args, rank, world, local, pg):
         per_tenant[k].append(i)
     start = time.perf_counter() + 0.5
     lock = threading.Lock()
+    from struct import unpack_from
+    samples = []  # (request, device bytes, image bytes, stored CRC): checked after the run
+
+    def sample_request(i, tk, kind, buf, used, rng):
+        """Two chunks of a completed request: the tenant's device bytes (which
+        stay as the request left them until the tenant's next request), the
+        image's or patch's bytes of that chunk and its stored CRC."""
+        out = []
+        sizes = tk["sizes"]
+        if kind == "incremental":
+            off, recs = 64, []
+            for n in sizes:  # walk the patch: record, hashes, dirty list, dirty chunks
+                nk = (n + UNIT - 1) // UNIT
+                dk = unpack_from("<Q", buf, off + 16)[0]
+                nd = unpack_from("<I", buf, off + 32 + 4 * nk)[0]
+                idx = np.frombuffer(buf, dtype="<u4", count=nd, offset=off + 36 + 4 * nk)
+                recs.append((off, dk, idx))
+                off = dk + sum((min(UNIT, n - int(c) * UNIT) + 4095) // 4096 * 4096 for c in idx)
+            cand = [k for k, (_, _, idx) in enumerate(recs) if idx.size]
+            for _ in range(2 if cand else 0):
+                k = cand[int(rng.integers(0, len(cand)))]
+                off, dk, idx = recs[k]
+                j = int(rng.integers(0, idx.size))
+                c = int(idx[j])
+                pos = dk + sum((min(UNIT, sizes[k] - int(x) * UNIT) + 4095) // 4096 * 4096 for x in idx[:j])
+                lo, hi = c * UNIT, min((c + 1) * UNIT, sizes[k])
+                out.append((i, tk["ts"][k][lo:hi].cpu().numpy(), buf[pos: pos + hi - lo].copy(),
+                            unpack_from("<I", buf, off + 32 + 4 * c)[0]))
+            return out
+        img = tk["full"]
+        for _ in range(2):
+            k = int(rng.integers(0, len(sizes)))
+            nk = (sizes[k] + UNIT - 1) // UNIT
+            if nk == 0:
+                continue
+            c = int(rng.integers(0, nk))
+            lo, hi = c * UNIT, min((c + 1) * UNIT, sizes[k])
+            d_off = unpack_from("<Q", img, tk["rec"][k] + 16)[0]
+            out.append((i, tk["ts"][k][lo:hi].cpu().numpy(), img[d_off + lo: d_off + hi].copy(),
+                        unpack_from("<I", img, tk["rec"][k] + 32 + 4 * c)[0]))
+        return out
 
     def tenant_loop(k):
         tk = T[k]
@@ -1168,6 +1214,10 @@ def run_serving(args, rank, world, local, pg):
                 status[i] = st_
                 moved[i] = tk["bytes"]
                 link[i] = int(stats["image_bytes"]) if kind == "incremental" else tk["bytes"]
+            if st_ == 0:
+                got = sample_request(i, tk, kind, buf, int(stats["image_bytes"]), np.random.default_rng(i))
+                with lock:
+                    samples.extend(got)
 
     th = [threading.Thread(target=tenant_loop, args=(k,)) for k in range(len(T))]
     t0 = time.perf_counter()
@@ -1177,6 +1227,14 @@ def run_serving(args, rank, world, local, pg):
         x.join()
     wall = time.perf_counter() - max(t0, start)
     sv.close()
+    # after the run: the sampled chunks against the oracle's CRC-32C and the
+    # device bytes
+    import oracle
+    bad = [i for i, d, im, h in samples if not (np.array_equal(d, im) and oracle.crc32c(d) == h)]
+    parity = {"requests_sampled": len(set(i for i, _, _, _ in samples)), "chunks_checked": len(samples),
+              "mismatches": len(bad),
+              "check": "per completed request, two chunks: the tenant's device bytes == the image's (or the "
+                       "patch's dirty-chunk) bytes, and the oracle's CRC-32C of them == the stored hash"}
     good = [l for l, s_ in zip(lat, status) if s_ == 0 and l is not None]
     gbs = sum(m_ for m_, s_ in zip(moved, status) if s_ == 0) / wall / 1e9
     link_gbs = sum(b_ for b_, s_ in zip(link, status) if s_ == 0) / wall / 1e9
@@ -1209,7 +1267,8 @@ def run_serving(args, rank, world, local, pg):
                              "%.1f GiB total), Poisson %.0f req/s, %d arrivals, full/incremental(5%%)/restore"
                              % (sum(tk["bytes"] for tk in T) / GiB, args.rate, len(reqs)),
                  "budgets": {"pinned": "64 GB", "hbm": "150 GB"}, "image": "pageable host memory"},
-                {"latency_ms": {"p50": float(np.percentile(good, 50)), "p99": float(np.percentile(good, 99)),
+                {"parity": parity,
+                 "latency_ms": {"p50": float(np.percentile(good, 50)), "p99": float(np.percentile(good, 99)),
                                 "max": float(max(good)), "completed": len(good), "failed": len(reqs) - len(good)},
                  "plain_serial_first_%d" % nb: ({"p50": float(np.percentile(plain_lat, 50)),
                                                  "p99": float(np.percentile(plain_lat, 99)),

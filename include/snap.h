@@ -109,6 +109,14 @@ typedef struct {
     double frozen_ms;        /* how long the caller was held: the whole call
                                 for synchronous calls; quiesce + cut for
                                 snap_checkpoint_async                     */
+    uint64_t device_errors;  /* error bits the kernels of the set's most
+                                recent call reported (that call returned
+                                SNAP_ECUDA), 0 if none: 1 = a bounded wait
+                                ran out, 2 = a tile outside its allocation
+                                table or misaligned, 4 = shared memory not
+                                where the CRC lookups expect it.  Unlike the
+                                other fields it is not the last successful
+                                call's. */
 } snap_stats;
 
 /* ------------------------------------------------------------------ sets */
@@ -348,10 +356,19 @@ typedef struct {
 /* Time the set's hash pass (mode SNAP_INCREMENTAL) or full gather (SNAP_FULL)
  * over a grid of launch shapes, adopt the fastest for this set, and record it
  * in the tuning cache keyed by (GPU name, operation, chunk size, state size
- * class); the cache file is $SNAP_TUNE_CACHE if set.  The device state is
- * read, never modified.  host_image (SNAP_FULL only) is a scratch image of
- * snap_image_bytes(FULL) bytes in snap_host_alloc memory. */
+ * class = floor(log2(state bytes))); the cache file is $SNAP_TUNE_CACHE if
+ * set (one JSON object per line, appended).  Every set reads that file when
+ * its layout is built (the first call after registering) and starts with the
+ * last shapes stored for its key, unless snap_opts.stages or hash_tma chose
+ * the shape.  The device state is read, never modified.  host_image
+ * (SNAP_FULL only) is a scratch image of snap_image_bytes(FULL) bytes in
+ * snap_host_alloc memory. */
 SNAP_API int snap_autotune(snap_set s, int mode, void *host_image, uint64_t cap, snap_tuning *out);
+
+/* The launch shape the set uses for mode (SNAP_FULL: the gather;
+ * SNAP_INCREMENTAL: the hash pass, which verify shares), after building its
+ * layout; *out->gbs is 0.  Errors: EINVAL, EBUSY, ENOMEM, ECUDA. */
+SNAP_API int snap_get_tuning(snap_set s, int mode, snap_tuning *out);
 
 /* ------------------------------------------------------------- serving */
 /* A request loop over many tenant sets: requests are admitted as pinned-host

@@ -37,7 +37,7 @@ EXPORTS = (
     "snap_checkpoint_file", "snap_restore_file", "snap_restore", "snap_restore_async", "snap_restore_ready", "snap_restore_wait", "snap_verify",
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
-    "snap_autotune", "snap_coordinate", "snap_checkpoint_coordinated", "snap_restore_coordinated",
+    "snap_autotune", "snap_get_tuning", "snap_coordinate", "snap_checkpoint_coordinated", "snap_restore_coordinated",
     "snap_link_ceiling",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
                 ("quiesce_ms", ctypes.c_double), ("hash_ms", ctypes.c_double),
                 ("diff_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
-                ("frozen_ms", ctypes.c_double)]
+                ("frozen_ms", ctypes.c_double), ("device_errors", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -127,6 +127,7 @@ def _lib():
             "snap_hash_chunks": [vp, u64, u64, vp, vp],
             "snap_hash_chunks_noalloc": [P(vp), P(u64), u32, u64, vp, vp],
             "snap_autotune": [vp, i32, vp, u64, P(Tuning)],
+            "snap_get_tuning": [vp, i32, P(Tuning)],
             "snap_coordinate": [P(CoordOps), vp],
             "snap_link_ceiling": [i32, i32, u64, i32, P(ctypes.c_double)],
             "snap_checkpoint_coordinated": [vp, vp, u64, i32, P(u64), AGREE_FN, vp],
@@ -371,6 +372,12 @@ class Set:
         _check(_lib().snap_autotune(self.h, mode, _addr(image) if image is not None else None,
                                     _nbytes(image) if image is not None else 0, ctypes.byref(t)),
                "snap_autotune")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    def tuning(self, mode: int = INCREMENTAL) -> dict:
+        """The launch shape the set uses for `mode` (snap_get_tuning)."""
+        t = Tuning()
+        _check(_lib().snap_get_tuning(self.h, mode, ctypes.byref(t)), "snap_get_tuning")
         return {k: getattr(t, k) for k, _ in t._fields_}
 
 

@@ -252,6 +252,21 @@ __device__ void drain(WarpCtx &w)
     }
 }
 
+// Test hook (Job.test_stall): take a stage and expect 16 bytes on its
+// mbarrier that no copy will deliver, then wait for it.  Nothing is in flight
+// for this warp at a tile's start (every chunk routine consumes the stages it
+// issues), so the barrier is the next one to consume; its bounded wait runs
+// out and the caller's error path (ERR_WAIT_TIMEOUT, drain, leave) runs with
+// no copy outstanding.
+__device__ bool stall_stage(WarpCtx &w)
+{
+    const uint32_t buf = issue_advance(w);
+    const uint32_t mb = w.mbar + 8 * buf;
+    if (w.lane == 0) mbar_arrive_tx(mb, 16u);
+    else mbar_arrive(mb);
+    return mbar_wait(w.mbar + 8 * w.cb, w.cpar);
+}
+
 // ------------------------------------------- segmented hash (HBM-bound path)
 // Lane l owns bytes [l*s, min((l+1)*s, L)) of the chunk; stage k holds the
 // next P bytes of every lane's segment in slot l (slot j at j*P).  Inside a
@@ -727,6 +742,15 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
         }
         bool ok = true;
         uint32_t h = 0;
+        if (jb.test_stall == tt + 1) {
+            ok = stall_stage(w);
+            if (ok && lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);  // cannot happen
+            if (!ok) {
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_WAIT_TIMEOUT);
+                drain(w);
+            }
+            break;
+        }
         switch (jb.op) {
         case OP_HASH:
         case OP_VERIFY:

@@ -428,6 +428,7 @@ int build_layout(snap_set_s *s)
         free_device(s);
         return cuda_status(e);
     }
+    adopt_cached_shapes(s);
     s->layout_dirty = false;
     return SNAP_OK;
 }
@@ -519,6 +520,16 @@ static void reset_call(snap_set_s *s, uint8_t *image, uint64_t cap)
     cb.cp.cap = cap;
 }
 
+// Test hook: SNAP_TEST_STALL_TILE=<n> (unset in normal use) makes the warp
+// that takes tile n of a direct full checkpoint's gather or of a verify wait
+// on a stage that no copy fills, so that the kernel's bounded wait runs out
+// and its error path runs.
+static uint64_t test_stall_tile()
+{
+    const char *e = std::getenv("SNAP_TEST_STALL_TILE");
+    return e && *e ? std::strtoull(e, nullptr, 10) + 1 : 0;
+}
+
 static Job base_job(const snap_set_s *s, uint32_t op)
 {
     Job j{};
@@ -530,6 +541,7 @@ static Job base_job(const snap_set_s *s, uint32_t op)
     j.op = op;
     j.layout = LAYOUT_IMAGE;
     j.res = &s->d_cb->res;
+    if (op == OP_GATHER || op == OP_VERIFY) j.test_stall = test_stall_tile();
     return j;
 }
 
@@ -575,6 +587,7 @@ static int finish(snap_set_s *s, double deadline)
         return rc;
     }
     if (rc) return rc;
+    s->device_err = s->h_res->err;
     if (s->h_res->err) return SNAP_ECUDA;
     return SNAP_OK;
 }
@@ -1364,6 +1377,7 @@ int snap_last_stats(snap_set s, snap_stats *out)
 {
     if (!s || !out) return SNAP_EINVAL;
     *out = s->last;
+    out->device_errors = s->device_err;
     return SNAP_OK;
 }
 

@@ -113,6 +113,7 @@ struct snap_set_s {
     uint64_t call_kernels = 0;  // kernels launched by the current call
 
     snapk::Ring *ring = nullptr;
+    uint64_t device_err = 0;  // kernel error bits (Result.err) of the most recent call
 
     // asynchronous checkpoint (async.cu)
     uint8_t *d_shadow = nullptr;                // packed copy of the state at the cut
@@ -183,6 +184,9 @@ int apply_patch_host(uint8_t *base, uint64_t base_len, const uint8_t *patch, uin
 // launch shapes (tune.cu)
 void default_shapes(snap_set_s *s);
 TileShape default_hash_shape(int ctas);
+// the shapes the tuning cache ($SNAP_TUNE_CACHE) holds for this set's
+// (GPU, operation, chunk size, state size class), adopted when its layout is built
+void adopt_cached_shapes(snap_set_s *s);
 
 // pageable images through the pinned ring (ring.cu)
 int ring_checkpoint(snap_set_s *s, ImageIO &io, uint64_t cap, int mode, uint64_t *used, double t0, double tq,

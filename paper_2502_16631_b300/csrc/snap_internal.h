@@ -83,6 +83,9 @@ struct Job {
     const uint64_t *dstart;        // OP_GATHER_DIRTY: per-allocation first dirty rank
     const unsigned long long *cap_exceeded;  // OP_GATHER_DIRTY: skip if set
     Result *res;                   // per-job counters (verify)
+    uint64_t test_stall;           // test hook, 0 in every normal call: the warp that takes
+                                   // tile test_stall - 1 waits on a stage no copy fills, so
+                                   // its bounded wait runs out (ERR_WAIT_TIMEOUT)
 };
 
 constexpr int kMaxJobs = 64;

@@ -6,9 +6,12 @@
 // autotuner times a set's own hash pass or full gather over a grid of
 // shapes that fit in shared memory, adopts the fastest, and appends it to a
 // cache file keyed by GPU name, operation, chunk size and state size class.
+// A set whose layout is built reads that file back and starts with the
+// shapes last stored for its key (explicit stage or TMA options win).
 #include "snap.h"
 #include "runtime_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -75,6 +78,74 @@ static void cache_store(const snap_set_s *s, int mode, const TileShape &t, doubl
     std::fclose(f);
 }
 
+// The shapes the autotuner can choose: a cached shape is adopted only if
+// it is one of them and fits the set's grid and shared memory.
+static const int kWarpsHash[] = {8, 12, 16, 20, 24, 32};
+static const int kWarpsGather[] = {2, 4, 8};
+static const int kStages[] = {2, 3, 4};
+static const int kPieceHash[] = {32, 64, 128};
+static const int kPieceGather[] = {128, 256};
+
+template <size_t N>
+static bool one_of(int v, const int (&l)[N])
+{
+    for (int x : l)
+        if (x == v) return true;
+    return false;
+}
+
+static bool valid_cached(const snap_set_s *s, int mode, const TileShape &t)
+{
+    const bool full = mode == SNAP_FULL;
+    if (full ? !one_of(t.warps, kWarpsGather) : !one_of(t.warps, kWarpsHash)) return false;
+    if (!one_of(t.stages, kStages)) return false;
+    if (full ? !one_of(t.piece, kPieceGather) : !one_of(t.piece, kPieceHash)) return false;
+    if (t.chains != 1 && !(t.chains == 2 && !full)) return false;
+    if (t.tma != 0 && !(t.tma == 1 && !full && t.chains == 1 && t.piece <= 128)) return false;
+    if (t.ctas != s->sms * ctas_per_sm(s)) return false;
+    return tile_smem_bytes(t) <= kMaxSmem;
+}
+
+// The shape last stored in the cache file for (GPU, mode, chunk, size class)
+// of this set, if any.
+static bool cache_lookup(const snap_set_s *s, int mode, TileShape *out)
+{
+    const std::string p = cache_path();
+    if (p.empty()) return false;
+    FILE *f = std::fopen(p.c_str(), "r");
+    if (!f) return false;
+    const int cls = size_class(s->total_bytes);
+    const std::string gpu = std::string("{\"gpu\": \"") + s->gpu_name + "\", ";
+    bool found = false;
+    char line[1024];
+    while (std::fgets(line, sizeof line, f)) {
+        if (std::strncmp(line, gpu.c_str(), gpu.size()) != 0) continue;
+        int op = -1, c = -1, w = 0, st = 0, pc = 0, ch = 0, tm = 0, ct = 0;
+        unsigned long long chunk = 0;
+        double gbs = 0;
+        if (std::sscanf(line + gpu.size(),
+                        "\"op\": %d, \"chunk\": %llu, \"class\": %d, \"warps\": %d, \"stages\": %d, \"piece\": %d, "
+                        "\"chains\": %d, \"tma\": %d, \"ctas\": %d, \"gbs\": %lf",
+                        &op, &chunk, &c, &w, &st, &pc, &ch, &tm, &ct, &gbs) != 10)
+            continue;
+        if (op != mode || chunk != s->C || c != cls) continue;
+        const TileShape t{w, st, pc, ct, ch, tm};
+        if (!valid_cached(s, mode, t)) continue;
+        *out = t;
+        found = true;  // keep reading: the last entry for the key wins
+    }
+    std::fclose(f);
+    return found;
+}
+
+void adopt_cached_shapes(snap_set_s *s)
+{
+    if (s->opts.stages || s->opts.hash_tma) return;  // the caller chose the shape
+    TileShape t{};
+    if (cache_lookup(s, SNAP_FULL, &t)) s->shape[SHAPE_GATHER] = t;
+    if (cache_lookup(s, SNAP_INCREMENTAL, &t)) s->shape[SHAPE_HASH] = t;
+}
+
 // Time one launch of a single-job tile kernel over the whole set.
 static int time_shape(snap_set_s *s, uint32_t op, uint8_t *dimg, const TileShape &t, double *ms)
 {
@@ -132,13 +203,8 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
     if (s->n_chunks == 0) return SNAP_EINVAL;
     const int kind = mode == SNAP_FULL ? SHAPE_GATHER : SHAPE_HASH;
     const uint32_t op = mode == SNAP_FULL ? OP_GATHER : OP_HASH;
-    static const int warps_h[] = {8, 12, 16, 20, 24, 32};
-    static const int warps_g[] = {2, 4, 8};
-    static const int stages_c[] = {2, 3, 4};
-    static const int piece_h[] = {32, 64, 128};
-    static const int piece_g[] = {128, 256};
-    const int *wl = mode == SNAP_FULL ? warps_g : warps_h;
-    const int *pl = mode == SNAP_FULL ? piece_g : piece_h;
+    const int *wl = mode == SNAP_FULL ? kWarpsGather : kWarpsHash;
+    const int *pl = mode == SNAP_FULL ? kPieceGather : kPieceHash;
     const int np = mode == SNAP_FULL ? 2 : 3;
     const int nch = mode == SNAP_FULL ? 1 : 2;
     const int cps = s->opts.ctas_per_sm ? (int)s->opts.ctas_per_sm : 1;
@@ -152,7 +218,7 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
                 for (int h = 1; h <= nch; ++h)
                 for (int tm = 0; tm <= (mode == SNAP_FULL || h == 2 || pl[c] > 128 ? 0 : 1); ++tm) {
                 // TMA staging exists for one chain per lane and pieces up to 128 bytes
-                TileShape t{wl[a], stages_c[b], pl[c], s->sms * cps, h, mode == SNAP_FULL ? 1 : tm};
+                TileShape t{wl[a], kStages[b], pl[c], s->sms * cps, h, mode == SNAP_FULL ? 1 : tm};
                 if (tile_smem_bytes(t) > kMaxSmem) continue;
                 double ms = 0, m2 = 0;
                 rc = time_shape(s, op, dimg, t, &ms);  // warm
@@ -192,5 +258,24 @@ extern "C" int snap_autotune(snap_set s, int mode, void *host_image, uint64_t ca
         out->chains = (uint32_t)best.chains;
         out->tma = (uint32_t)best.tma;
     }
+    return SNAP_OK;
+}
+
+extern "C" int snap_get_tuning(snap_set s, int mode, snap_tuning *out)
+{
+    if (!s || !out || (mode != SNAP_FULL && mode != SNAP_INCREMENTAL)) return SNAP_EINVAL;
+    BusyGuard g(s);
+    if (!g.ok) return SNAP_EBUSY;
+    cudaSetDevice(s->device);
+    const int rc = build_layout(s);  // a fresh layout adopts cached shapes
+    if (rc) return rc;
+    const TileShape &t = s->shape[mode == SNAP_FULL ? SHAPE_GATHER : SHAPE_HASH];
+    std::memset(out, 0, sizeof *out);
+    out->warps = (uint32_t)t.warps;
+    out->stages = (uint32_t)t.stages;
+    out->piece_bytes = (uint32_t)t.piece;
+    out->ctas_per_sm = (uint32_t)(t.ctas / std::max(1, s->sms));
+    out->chains = (uint32_t)t.chains;
+    out->tma = (uint32_t)t.tma;
     return SNAP_OK;
 }

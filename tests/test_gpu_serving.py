@@ -26,10 +26,27 @@ def tenant_sizes(t):
     return [int(x) for x in rng.integers(1, 6 * MiB, 6)] + [C * 3]
 
 
-def make_tenants(n, seed):
+# Large-request case: tenants 0, 2 and 4 hold about 700 MiB in ten
+# allocations, so with a 1 GiB staging pool (16 slots of 64 MiB) each of
+# their full checkpoints, incremental checkpoints (most chunks dirty) and
+# restores spans more windows than the scheduler gives one request per round
+# (8); the other tenants stay small.
+BIG_TENANTS = (0, 2, 4)
+BIG_POOL = 1 << 30
+BIG_SLOT = 64 * MiB
+
+
+def big_tenant_sizes(t):
+    rng = np.random.default_rng(200 + t)
+    if t in BIG_TENANTS:
+        return [int(x) // 16 * 16 + 16 * (k % 3) + 1 for k, x in enumerate(rng.integers(40 * MiB, 100 * MiB, 10))]
+    return [int(x) for x in rng.integers(1, 6 * MiB, 4)] + [C * 3]
+
+
+def make_tenants(n, seed, sizes_of=tenant_sizes):
     tenants = []
     for t in range(n):
-        sizes = tenant_sizes(t)
+        sizes = sizes_of(t)
         ts = []
         for k, nbytes in enumerate(sizes):
             d = torch.empty(nbytes + 16, dtype=torch.uint8, device="cuda")[:nbytes]
@@ -59,16 +76,40 @@ def mutate(ts, seed):
     torch.cuda.synchronize()
 
 
+def mutate_most(ts, seed):
+    """Every chunk but each tenth changes in every byte (and every ragged
+    last chunk): most of the tenant is dirty."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    for d in ts:
+        nf = d.numel() // C
+        if nf:
+            rows = d[: nf * C].view(nf, C)
+            idx = torch.tensor([i for i in range(nf) if i % 10], dtype=torch.long, device="cuda")
+            if idx.numel():
+                rows[idx] ^= torch.randint(1, 256, (idx.numel(), C), dtype=torch.uint8, device="cuda", generator=g)
+        if d.numel() > nf * C:
+            tail = d[nf * C:]
+            tail ^= torch.randint(1, 256, (tail.numel(),), dtype=torch.uint8, device="cuda", generator=g)
+    torch.cuda.synchronize()
+
+
 PINNED = (0, 3, 4)  # tenants whose images are pinned (direct windows) when pinned=True
 
 
-def scenario(mixed: bool, pinned: bool = False):
+def scenario(mixed: bool, pinned: bool = False, big: bool = False):
     """Phase 1: full checkpoints of 6 tenants; phase 2: incremental (t0, t1),
     full (t2, t3), restore of the phase-1 image after scribbling (t4, t5).
     With `pinned`, the images of tenants PINNED are registered, so the server
-    reads and writes them directly, and the others stay pageable (staged)."""
-    tenants = make_tenants(6, seed=500)
-    sv = snap.Server(pinned_budget=64 * MiB, hbm_budget=1 << 40, chunk_bytes=C)
+    reads and writes them directly, and the others stay pageable (staged).
+    With `big`, tenants BIG_TENANTS are large, tenant 0's incremental finds
+    most chunks dirty, and the staging pool is BIG_POOL."""
+    if big:
+        tenants = make_tenants(6, seed=550, sizes_of=big_tenant_sizes)
+        sv = snap.Server(pinned_budget=BIG_POOL, hbm_budget=1 << 40, chunk_bytes=C, ring_bytes=BIG_POOL)
+    else:
+        tenants = make_tenants(6, seed=500)
+        sv = snap.Server(pinned_budget=64 * MiB, hbm_budget=1 << 40, chunk_bytes=C)
     imgs = [np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8) for s, _ in tenants]
     patches = [np.full(s.image_bytes(snap.INCREMENTAL), 0x5A, dtype=np.uint8) for s, _ in tenants]
     registered = []
@@ -92,7 +133,10 @@ def scenario(mixed: bool, pinned: bool = False):
     stats1 = run([(s, snap.REQ_FULL, imgs[t]) for t, (s, _) in enumerate(tenants)])
     out["full1"] = [imgs[t][: stats1[t]["image_bytes"]].copy() for t in range(6)]
     for t in (0, 1, 2, 3):
-        mutate(tenants[t][1], seed=900 + t)
+        if big and t == 0:
+            mutate_most(tenants[t][1], seed=900 + t)
+        else:
+            mutate(tenants[t][1], seed=900 + t)
     for t in (4, 5):
         for d in tenants[t][1]:
             d.fill_(0x33)
@@ -118,9 +162,19 @@ def scenario(mixed: bool, pinned: bool = False):
 
 
 @pytest.mark.parametrize("pinned", [False, True])
-def test_serving_mix_equals_alone_equals_oracle(pinned):
-    mixed = scenario(mixed=True, pinned=pinned)
-    alone = scenario(mixed=False, pinned=pinned)
+@pytest.mark.parametrize("big", [False, True])
+def test_serving_mix_equals_alone_equals_oracle(pinned, big):
+    """Alone == in the mix == oracle, with small tenants, and (big) with
+    full, incremental and restore requests that each span more windows than
+    one request may put into a round, so that the per-request round cap and
+    the shortest-remaining-first order act while they run."""
+    if big:
+        for t in BIG_TENANTS:
+            state = sum(big_tenant_sizes(t))
+            assert state > 8 * BIG_SLOT  # more windows than the round cap, staged or direct
+            assert 0.8 * state > 8 * BIG_SLOT  # the dirty windows of tenant 0's incremental too
+    mixed = scenario(mixed=True, pinned=pinned, big=big)
+    alone = scenario(mixed=False, pinned=pinned, big=big)
     for key in ("full1", "incr", "full2"):
         for a, b in zip(mixed[key], alone[key]):
             assert np.array_equal(a, b), key

@@ -450,6 +450,109 @@ def test_autotune_every_shape_agrees_then_parity(C):
     assert nd == 2 and np.array_equal(patch.view(used_p), exp)
 
 
+def _shape(t):
+    return tuple(t[k] for k in ("warps", "stages", "piece_bytes", "chains", "tma", "ctas_per_sm"))
+
+
+def test_autotune_cache_is_read_back(tmp_path, monkeypatch):
+    """A set tuned once stores its winners in $SNAP_TUNE_CACHE; a new set of
+    the same GPU, chunk size and state size class starts with those shapes,
+    and its images still equal the oracle's.  A hand-written entry with a
+    shape no default uses is adopted the same way; an entry for another size
+    class, or an invalid shape, is not."""
+    import math
+    C = 65536
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("SNAP_TUNE_CACHE", str(cache))
+    sizes = [8 * C, 3 * C + 4096 + 16, 100000, 12345, C]
+    ts, hs = device_state(sizes, seed=35)
+    a = make_set(ts, C)
+    img = snap.HostBuffer(a.image_bytes(snap.FULL))
+    t_inc = a.autotune(snap.INCREMENTAL)
+    t_full = a.autotune(snap.FULL, img)
+    assert cache.exists() and len(cache.read_text().splitlines()) == 2
+    ts2, hs2 = device_state(sizes, seed=36)
+    b = make_set(ts2, C)
+    assert _shape(b.tuning(snap.INCREMENTAL)) == _shape(t_inc)
+    assert _shape(b.tuning(snap.FULL)) == _shape(t_full)
+    img2 = snap.HostBuffer(b.image_bytes(snap.FULL))
+    used = b.checkpoint(img2, snap.FULL)
+    assert np.array_equal(img2.view(used), oracle.write_full(hs2, C, 0)[1])
+    patch = snap.HostBuffer(b.image_bytes(snap.INCREMENTAL))
+    mutate(ts2, C, [(0, 5), (2, 1)])
+    used_p = b.checkpoint(patch, snap.INCREMENTAL)
+    rc, exp, nd = oracle.write_patch(readback(ts2), C, [oracle.chunk_hashes(h, C) for h in hs2], 1, 0)
+    assert nd == 2 and np.array_equal(patch.view(used_p), exp)
+    # a hand-written entry: 16 warps, 3 stages, 32-byte pieces for the hash
+    # pass (the default is 24 / 2 / 64), appended after the tuned one
+    gpu = torch.cuda.get_device_name()
+    cls = int(math.floor(math.log2(sum(sizes))))
+    ctas = torch.cuda.get_device_properties(0).multi_processor_count
+    entry = ('{"gpu": "%s", "op": 1, "chunk": %d, "class": %d, "warps": 16, "stages": 3, "piece": 32, '
+             '"chains": 1, "tma": 0, "ctas": %d, "gbs": 1.0}\n')
+    with open(cache, "a") as f:
+        f.write(entry % (gpu, C, cls + 1, ctas))  # another size class: ignored
+        f.write(entry.replace('"warps": 16', '"warps": 7') % (gpu, C, cls, ctas))  # not a tunable shape
+        f.write(entry % (gpu, C, cls, ctas))
+    ts3, hs3 = device_state(sizes, seed=37)
+    c = make_set(ts3, C)
+    t3 = c.tuning(snap.INCREMENTAL)
+    assert (t3["warps"], t3["stages"], t3["piece_bytes"], t3["chains"], t3["tma"]) == (16, 3, 32, 1, 0)
+    assert _shape(c.tuning(snap.FULL)) == _shape(t_full)
+    used = c.checkpoint(img2, snap.FULL)
+    assert np.array_equal(img2.view(used), oracle.write_full(hs3, C, 0)[1])
+    assert c.verify(img2, used) == 0
+    # without the cache file a new set keeps the defaults
+    monkeypatch.delenv("SNAP_TUNE_CACHE")
+    d = make_set(ts3, C)
+    t4 = d.tuning(snap.INCREMENTAL)
+    assert (t4["warps"], t4["stages"], t4["piece_bytes"]) == (24, 2, 64)
+    for x in (a, b, c, d):
+        x.close()
+
+
+def test_device_wait_gives_up_and_the_set_recovers(monkeypatch):
+    """The kernels' own give-up path, reached without a fault: with the test
+    hook SNAP_TEST_STALL_TILE the warp that takes that tile waits on a stage
+    whose bytes no copy delivers, so its bounded mbarrier wait (2 s) runs
+    out; it records ERR_WAIT_TIMEOUT, drains and leaves, every other warp
+    leaves at its next tile, and the call returns SNAP_ECUDA well inside the
+    call deadline with nothing committed (Sec. 3.1.1: a lock that times out
+    rolls back).  Checked on a full checkpoint (general kernel) and on verify
+    (the hash-only kernel); the next calls succeed and match the oracle."""
+    import time
+    C = 65536
+    sizes = [40 * C + 100, 3 * C, 12345]
+    ts, hs = device_state(sizes, seed=71)
+    s = make_set(ts, C)
+    nch = sum((n + C - 1) // C for n in sizes)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    used = s.checkpoint(full, snap.FULL)
+    base, gen = s.committed_hashes(nch)
+    base = base.copy()
+    assert s.stats()["device_errors"] == 0
+    mutate(ts, C, [(0, 7), (2, 0)])
+    cur = readback(ts)
+    img2 = snap.HostBuffer(s.image_bytes(snap.FULL))
+    monkeypatch.setenv("SNAP_TEST_STALL_TILE", "5")
+    t0 = time.perf_counter()
+    rc, _ = s.checkpoint_status(img2, snap.FULL)
+    dt = time.perf_counter() - t0
+    assert rc == snap.ECUDA and s.stats()["device_errors"] == 1
+    assert dt < 8.0  # two bounded waits of the stalled warp; the call deadline is 10 s
+    b2, g2 = s.committed_hashes(nch)
+    assert g2 == gen and np.array_equal(b2, base)
+    with pytest.raises(snap.SnapError) as e:
+        s.verify(full, used)
+    assert e.value.status == snap.ECUDA and s.stats()["device_errors"] == 1
+    monkeypatch.delenv("SNAP_TEST_STALL_TILE")
+    used2 = s.checkpoint(img2, snap.FULL)
+    assert s.stats()["device_errors"] == 0
+    assert np.array_equal(img2.view(used2), oracle.write_full(cur, C, 1)[1])
+    assert s.verify(img2, used2) == 0
+    s.close()
+
+
 def test_stats_report_phases():
     ts, _ = device_state([64 * 65536], seed=32)
     s = make_set(ts, 65536)
