@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--serve-pool-gib", type=int, default=24, help="serving: pinned staging pool (GiB, within "
                    "the 64 GB pinned budget)")
     p.add_argument("--no-plain", action="store_true", help="serving: skip the serial plain-copy comparison")
+    p.add_argument("--serve-lower-rates", default="12", help="serving: further arrival rates (comma-separated) "
+                   "run for context after the main one, each over half the main run's span")
     p.add_argument("--serve-pin-gb", type=float, default=0.0, help="serving: GB of tenant images to pin "
                    "(snap_host_register) for direct access, within the 64 GB pinned budget beside the pool "
                    "(default 0: measured slower under this mix)")
@@ -1094,17 +1096,18 @@ def run_serving(args, rank, world, local, pg):
         T.append({"set": s, "ts": ts, "full": full, "patch": patch, "bytes": sum(sizes), "units": nunits,
                   "has_image": False, "sizes": sizes, "rec": rec})
     torch.cuda.synchronize()
-    # arrivals
-    r = workloads.Rng(args.seed ^ 0xA77)
-    t, reqs = 0.0, []
-    legal = [{"full"} for _ in T]
-    for i in range(args.arrivals):
-        t += -np.log(1.0 - r.uniform()) / args.rate
-        k = r.randint(0, len(T) - 1)
-        kinds = sorted(legal[k])
-        kind = kinds[r.randint(0, len(kinds) - 1)]
-        reqs.append((t, k, kind))
-        legal[k] |= {"incremental", "restore"}
+    def arrivals(rate, n, seed):
+        r = workloads.Rng(seed)
+        t, reqs = 0.0, []
+        legal = [{"full"} for _ in T]
+        for i in range(n):
+            t += -np.log(1.0 - r.uniform()) / rate
+            k = r.randint(0, len(T) - 1)
+            kinds = sorted(legal[k])
+            kind = kinds[r.randint(0, len(kinds) - 1)]
+            reqs.append((t, k, kind))
+            legal[k] |= {"incremental", "restore"}
+        return reqs
 
     def mutate(tk, seed):
         """5 % of each allocation's whole 64 KiB units, every byte changed."""
@@ -1134,21 +1137,9 @@ def run_serving(args, rank, world, local, pg):
         pinned_tenants.append(k)
         pin_left -= need
     t_pin = time.perf_counter() - t_pin
-    sv = snap.Server(pinned_budget=64 * 10 ** 9, hbm_budget=150 * 10 ** 9, chunk_bytes=UNIT,
-                     ring_bytes=args.serve_pool_gib * GiB)
-    lat = [None] * len(reqs)
-    moved = [0] * len(reqs)
-    link = [0] * len(reqs)  # bytes over the host link: image or patch written, or image restored
-    status = [0] * len(reqs)
-    per_tenant = [[] for _ in T]
-    for i, (ta, k, kind) in enumerate(reqs):
-        per_tenant[k].append(i)
-    start = time.perf_counter() + 0.5
-    lock = threading.Lock()
     from struct import unpack_from
-    samples = []  # (request, device bytes, image bytes, stored CRC): checked after the run
 
-    def sample_request(i, tk, kind, buf, used, rng):
+    def sample_request(i, tk, kind, buf, rng):
         """Two chunks of a completed request: the tenant's device bytes (which
         stay as the request left them until the tenant's next request), the
         image's or patch's bytes of that chunk and its stored CRC."""
@@ -1187,60 +1178,98 @@ def run_serving(args, rank, world, local, pg):
                         unpack_from("<I", img, tk["rec"][k] + 32 + 4 * c)[0]))
         return out
 
-    def tenant_loop(k):
-        tk = T[k]
-        torch.cuda.set_device(local)
-        for i in per_tenant[k]:
-            ta, _, kind = reqs[i]
-            # the tenant's own work between its requests (before the arrival)
-            if kind == "incremental":
-                mutate(tk, 7 * i + 1)
-                rk, buf = snap.REQ_INCREMENTAL, tk["patch"]
-            elif kind == "restore":
-                for x in tk["ts"]:
-                    x.fill_(0x33)  # scribble: the restore must bring the image back
-                torch.cuda.synchronize()
-                rk, buf = snap.REQ_RESTORE, tk["full"]
-            else:
-                rk, buf = snap.REQ_FULL, tk["full"]
-            delay = start + ta - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            ticket = sv.submit(tk["set"], rk, buf)
-            rc, st_, stats = sv.wait(ticket, 600000)
-            done = time.perf_counter()
-            with lock:
-                lat[i] = (done - (start + ta)) * 1e3
-                status[i] = st_
-                moved[i] = tk["bytes"]
-                link[i] = int(stats["image_bytes"]) if kind == "incremental" else tk["bytes"]
-            if st_ == 0:
-                got = sample_request(i, tk, kind, buf, int(stats["image_bytes"]), np.random.default_rng(i))
-                with lock:
-                    samples.extend(got)
+    def simulate(reqs, tag):
+        """Run the arrivals `reqs` against a fresh server; per-request
+        latency (arrival to completion), status, bytes, and sampled chunks."""
+        sv = snap.Server(pinned_budget=64 * 10 ** 9, hbm_budget=150 * 10 ** 9, chunk_bytes=UNIT,
+                         ring_bytes=args.serve_pool_gib * GiB)
+        lat = [None] * len(reqs)
+        moved = [0] * len(reqs)
+        link = [0] * len(reqs)  # bytes over the host link: image or patch written, or image restored
+        status = [0] * len(reqs)
+        samples = []  # (request, device bytes, image bytes, stored CRC): checked after the run
+        per_tenant = [[] for _ in T]
+        for i, (ta, k, kind) in enumerate(reqs):
+            per_tenant[k].append(i)
+        start = time.perf_counter() + 0.5
+        lock = threading.Lock()
 
-    th = [threading.Thread(target=tenant_loop, args=(k,)) for k in range(len(T))]
-    t0 = time.perf_counter()
-    for x in th:
-        x.start()
-    for x in th:
-        x.join()
-    wall = time.perf_counter() - max(t0, start)
-    sv.close()
-    # after the run: the sampled chunks against the oracle's CRC-32C and the
+        def tenant_loop(k):
+            tk = T[k]
+            torch.cuda.set_device(local)
+            for i in per_tenant[k]:
+                ta, _, kind = reqs[i]
+                # the tenant's own work between its requests (before the arrival)
+                if kind == "incremental":
+                    mutate(tk, 7 * i + 1 + tag)
+                    rk, buf = snap.REQ_INCREMENTAL, tk["patch"]
+                elif kind == "restore":
+                    for x in tk["ts"]:
+                        x.fill_(0x33)  # scribble: the restore must bring the image back
+                    torch.cuda.synchronize()
+                    rk, buf = snap.REQ_RESTORE, tk["full"]
+                else:
+                    rk, buf = snap.REQ_FULL, tk["full"]
+                delay = start + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                ticket = sv.submit(tk["set"], rk, buf)
+                rc, st_, stats = sv.wait(ticket, 600000)
+                done = time.perf_counter()
+                with lock:
+                    lat[i] = (done - (start + ta)) * 1e3
+                    status[i] = st_
+                    moved[i] = tk["bytes"]
+                    link[i] = int(stats["image_bytes"]) if kind == "incremental" else tk["bytes"]
+                if st_ == 0:
+                    got = sample_request(i, tk, kind, buf, np.random.default_rng(i + tag))
+                    with lock:
+                        samples.extend(got)
+
+        th = [threading.Thread(target=tenant_loop, args=(k,)) for k in range(len(T))]
+        t0 = time.perf_counter()
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        wall = time.perf_counter() - max(t0, start)
+        sv.close()
+        good = [l for l, s_ in zip(lat, status) if s_ == 0 and l is not None]
+        return {"lat": lat, "status": status, "good": good, "wall": wall, "samples": samples,
+                "gbs": sum(m_ for m_, s_ in zip(moved, status) if s_ == 0) / wall / 1e9,
+                "link_gbs": sum(b_ for b_, s_ in zip(link, status) if s_ == 0) / wall / 1e9,
+                "offered_gbs": (sum(T[k]["bytes"] for _, k, kind in reqs if kind != "incremental")
+                                + sum(0.05 * T[k]["bytes"] for _, k, kind in reqs if kind == "incremental"))
+                               / reqs[-1][0] / 1e9}
+
+    reqs = arrivals(args.rate, args.arrivals, args.seed ^ 0xA77)
+    main = simulate(reqs, 0)
+    lower = []
+    for rate in [float(x) for x in args.serve_lower_rates.split(",") if x.strip()]:
+        n_low = max(1, int(round(args.arrivals * rate / args.rate / 2)))  # half the span of the main run
+        low = simulate(arrivals(rate, n_low, (args.seed ^ 0xA77) + int(rate * 100)), 1 << 20)
+        lower.append({"rate": rate, "arrivals": n_low, "p50": float(np.percentile(low["good"], 50)),
+                      "p99": float(np.percentile(low["good"], 99)), "completed": len(low["good"]),
+                      "gbs": low["gbs"], "link_gbs": low["link_gbs"], "offered_link_gbs": low["offered_gbs"]})
+        main["samples"].extend(low["samples"])
+    lat, status, good, wall, samples = main["lat"], main["status"], main["good"], main["wall"], main["samples"]
+    gbs, link_gbs, offered_gbs = main["gbs"], main["link_gbs"], main["offered_gbs"]
+    # after the runs: the sampled chunks against the oracle's CRC-32C and the
     # device bytes
     import oracle
     bad = [i for i, d, im, h in samples if not (np.array_equal(d, im) and oracle.crc32c(d) == h)]
     parity = {"requests_sampled": len(set(i for i, _, _, _ in samples)), "chunks_checked": len(samples),
               "mismatches": len(bad),
-              "check": "per completed request, two chunks: the tenant's device bytes == the image's (or the "
-                       "patch's dirty-chunk) bytes, and the oracle's CRC-32C of them == the stored hash"}
-    good = [l for l, s_ in zip(lat, status) if s_ == 0 and l is not None]
-    gbs = sum(m_ for m_, s_ in zip(moved, status) if s_ == 0) / wall / 1e9
-    link_gbs = sum(b_ for b_, s_ in zip(link, status) if s_ == 0) / wall / 1e9
-    offered_gbs = (sum(T[k]["bytes"] for _, k, kind in reqs if kind != "incremental")
-                   + sum(0.05 * T[k]["bytes"] for _, k, kind in reqs if kind == "incremental")) / reqs[-1][0] / 1e9
+              "check": "per completed request (every run), two chunks: the tenant's device bytes == the image's "
+                       "(or the patch's dirty-chunk) bytes, and the oracle's CRC-32C of them == the stored hash"}
     both = link_peak_both(torch)
+    workers = min(32, max(2, os.cpu_count() or 2))  # the server's copy workers (one per host thread)
+    hc = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3)
+    hc_link = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3, with_link=True)
+    # a staged byte costs host DRAM a read and a write for the copy plus one
+    # access for the link transfer; the copy probe moves 2 DRAM bytes per byte
+    host_bound = 2.0 * hc / 3.0
+    peak = min(both["sm_both"], host_bound)
     # serial plain full copies of the same arrivals (FIFO single server; each
     # request's service time measured by running it, start = max(arrival,
     # previous end)); the first 240 arrivals
@@ -1270,17 +1299,23 @@ def run_serving(args, rank, world, local, pg):
                 {"parity": parity,
                  "latency_ms": {"p50": float(np.percentile(good, 50)), "p99": float(np.percentile(good, 99)),
                                 "max": float(max(good)), "completed": len(good), "failed": len(reqs) - len(good)},
+                 "latency_at_lower_rates": lower,
                  "plain_serial_first_%d" % nb: ({"p50": float(np.percentile(plain_lat, 50)),
                                                  "p99": float(np.percentile(plain_lat, 99)),
                                                  "ours_p50": float(np.percentile(ours_prefix, 50)),
                                                  "ours_p99": float(np.percentile(ours_prefix, 99))} if nb else None),
-                 "roofline": {"bound": "host_link (both directions)", "kernel": "serving rounds (mixed gather + "
-                              "scatter launches) + host copies", "achieved": link_gbs, "peak": both["sm_both"],
-                              "unit": "GB/s", "frac": link_gbs / both["sm_both"], "ce_both": both["ce_both"],
-                              "offered": offered_gbs,
+                 "roofline": {"bound": "host_memory" if host_bound < both["sm_both"] else "host_link (both directions)",
+                              "kernel": "serving rounds (mixed gather + scatter launches) + host copies",
+                              "achieved": link_gbs, "peak": peak, "unit": "GB/s", "frac": link_gbs / peak,
+                              "link_peak_both": both["sm_both"], "ce_both": both["ce_both"],
+                              "host_copy_gbs": hc, "host_copy_gbs_under_link_load": hc_link,
+                              "host_memory_bound": host_bound, "copy_workers": workers, "offered": offered_gbs,
                               "note": "achieved = image, patch and restore bytes over the link / wall time; peak = "
-                                      "SM loads/stores in both directions at once (snap_link_ceiling 2); offered = "
-                                      "the arrivals' link bytes / arrival span (patches at 5 %)"},
+                                      "min(SM loads/stores in both directions at once (snap_link_ceiling 2), "
+                                      "2/3 x the workers' pinned<->pageable copy rate (snap_host_copy_ceiling 2): "
+                                      "every staged byte is one host copy (a DRAM read and write) plus one link "
+                                      "transfer (a DRAM access)); offered = the arrivals' link bytes / arrival "
+                                      "span (patches at 5 %)"},
                  "staging_pool_gib": args.serve_pool_gib,
                  "pinned_tenants": {"count": len(pinned_tenants),
                                     "gb": sum(T[k]["full"].nbytes + T[k]["patch"].nbytes for k in pinned_tenants) / 1e9,

@@ -341,6 +341,24 @@ SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *
  * current device.  Errors: EINVAL, ENOMEM, ECUDA. */
 SNAP_API int snap_link_ceiling(int device, int direction, uint64_t bytes, int reps, double *gbs);
 
+/* Measure the host-memory side of staged transfers: `threads` host threads
+ * copy `bytes` (rounded down to 4 KiB) between a pinned, mapped buffer and a
+ * pageable one with the copy routine the ring and the server's workers use
+ * (streaming stores) -- direction 0: pinned to pageable (a checkpoint
+ * draining its slots), 1: pageable to pinned (a restore filling them), 2:
+ * half the threads each way at once, *gbs counting both directions' bytes.
+ * With with_link != 0 the GPU meanwhile moves bytes over the host link in
+ * both directions with SM loads and stores (the host DRAM traffic the copies
+ * share in the serving loop).  Best of `reps` rounds after a warm-up round.
+ * Every byte staged through a slot costs host DRAM a read and a write for the
+ * copy plus one access for the link transfer, so this bounds what staged
+ * (pageable-image) checkpoints and restores can sustain.  Allocates and frees
+ * `bytes` (twice that for direction 2) of pinned and of pageable memory, and
+ * 2 GiB of each more with with_link, on the current device.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+SNAP_API int snap_host_copy_ceiling(int threads, int direction, uint64_t bytes, int reps, int with_link,
+                                    double *gbs);
+
 /* ----------------------------------------------------------- autotuning */
 typedef struct {
     uint32_t warps;        /* warps per CTA of the persistent kernel */

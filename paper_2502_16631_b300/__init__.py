@@ -38,7 +38,7 @@ EXPORTS = (
     "snap_apply_patch", "snap_committed_hashes", "snap_last_stats", "snap_strerror",
     "snap_plain_checkpoint", "snap_plain_restore", "snap_hash_chunks", "snap_hash_chunks_noalloc",
     "snap_autotune", "snap_get_tuning", "snap_coordinate", "snap_checkpoint_coordinated", "snap_restore_coordinated",
-    "snap_link_ceiling",
+    "snap_link_ceiling", "snap_host_copy_ceiling",
     "snap_server_create", "snap_server_destroy", "snap_server_submit", "snap_server_wait",
 )
 
@@ -130,6 +130,7 @@ def _lib():
             "snap_get_tuning": [vp, i32, P(Tuning)],
             "snap_coordinate": [P(CoordOps), vp],
             "snap_link_ceiling": [i32, i32, u64, i32, P(ctypes.c_double)],
+            "snap_host_copy_ceiling": [i32, i32, u64, i32, i32, P(ctypes.c_double)],
             "snap_checkpoint_coordinated": [vp, vp, u64, i32, P(u64), AGREE_FN, vp],
             "snap_restore_coordinated": [vp, u64, vp, AGREE_FN, vp],
             "snap_server_create": [P(vp), u64, u64, P(Opts)],
@@ -435,6 +436,17 @@ def host_register(array: np.ndarray) -> None:
 def host_unregister(array: np.ndarray) -> None:
     """Undo host_register (before the array is freed)."""
     _check(_lib().snap_host_unregister(array.ctypes.data), "snap_host_unregister")
+
+
+def host_copy_ceiling(threads: int, direction: int = 2, nbytes: int = 2 << 30, reps: int = 3,
+                      with_link: bool = False) -> float:
+    """GB/s that `threads` host threads copy between pinned and pageable
+    memory with the workers' copy routine (0: pinned to pageable, 1: the
+    other way, 2: both at once), optionally under link load."""
+    v = ctypes.c_double()
+    _check(_lib().snap_host_copy_ceiling(threads, direction, nbytes, reps, 1 if with_link else 0, ctypes.byref(v)),
+           "snap_host_copy_ceiling")
+    return v.value
 
 
 def link_ceiling(direction: int = 0, nbytes: int = 1 << 30, reps: int = 3, device: int = -1) -> float:

@@ -252,7 +252,11 @@ static void free_device(snap_set_s *s)
 static void plan_groups(snap_set_s *s)
 {
     const uint64_t kGroupBytes = std::max<uint64_t>(64ull << 20, 4096 * s->C);
-    s->n_groups = (int)std::min<uint64_t>((uint64_t)kMaxGroups, s->total_bytes / kGroupBytes);
+    uint64_t cap = kMaxGroups;
+    // SNAP_PIPE_GROUPS: a different stage cap (2 .. kMaxPipe), for measurements
+    if (const char *e = std::getenv("SNAP_PIPE_GROUPS"))
+        cap = std::max<uint64_t>(2, std::min<uint64_t>((uint64_t)kMaxPipe, std::strtoull(e, nullptr, 10)));
+    s->n_groups = (int)std::min<uint64_t>(cap, s->total_bytes / kGroupBytes);
 }
 
 // The stages of a pipelined incremental checkpoint for hash launches of W

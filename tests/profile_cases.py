@@ -6,6 +6,9 @@ under `ncu`; not collected by pytest).
     python tests/profile_cases.py hash [reps]     # 1 GiB chunk hasher
     python tests/profile_cases.py cut [reps]      # 8 x 64 MiB, asynchronous checkpoints
                                                   # (k_shadow_copy is the cut)
+    python tests/profile_cases.py ring [reps]     # 8 x 256 MiB, full checkpoints through the
+                                                  # 4 GiB ring into a pageable image (32 gather
+                                                  # launches of one 64 MiB window each)
 """
 import os
 import sys
@@ -22,7 +25,18 @@ MiB = 1 << 20
 def main():
     op = sys.argv[1]
     reps = int(sys.argv[2]) if len(sys.argv) > 2 else 2
-    if op == "hash":
+    if op == "ring":
+        import numpy as np
+        ts = [torch.empty(256 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]
+        for t in ts:
+            t.random_(0, 256)
+        s = snap.Set(chunk_bytes=65536, ring_bytes=4096 * MiB)
+        for t in ts:
+            s.register(t)
+        img = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
+        for _ in range(reps + 1):
+            s.checkpoint(img, snap.FULL)
+    elif op == "hash":
         x = torch.empty(1024 * MiB, dtype=torch.uint8, device="cuda")
         x.random_(0, 256)
         h = torch.empty(1024 * MiB // 65536, dtype=torch.int32, device="cuda")
