@@ -83,7 +83,9 @@ typedef struct {
                               legacy default stream */
     uint32_t ctas_per_sm;  /* persistent CTAs per SM; 0 = tuned default */
     uint32_t stages;       /* staging buffers per warp; 0 = tuned default */
-    uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB */
+    uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB
+                              (its host copy workers: min(12, host threads
+                              - 2), or $SNAP_RING_WORKERS) */
     uint32_t async_ctas;   /* CTAs of the background part of snap_checkpoint_async;
                               default 8 (enough to saturate the host link) */
     uint32_t hash_tma;     /* 1: stage the hash pass with 2D TMA tensor copies

@@ -6,6 +6,7 @@
 // else AVX2, else memcpy; unaligned heads and tails go through memcpy.
 #pragma once
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #include <immintrin.h>
 
@@ -62,7 +63,12 @@ inline void stream_copy(void *dst, const void *src, uint64_t n)
         s += head;
         n -= head;
     }
-    static const int level = __builtin_cpu_supports("avx512f") ? 2 : (__builtin_cpu_supports("avx2") ? 1 : 0);
+    // SNAP_COPY_NT=0 selects plain memcpy (cached stores), for measurements
+    static const int level = [] {
+        const char *e = getenv("SNAP_COPY_NT");
+        if (e && e[0] == '0') return 0;
+        return __builtin_cpu_supports("avx512f") ? 2 : (__builtin_cpu_supports("avx2") ? 1 : 0);
+    }();
     if (level == 2) stream_copy_avx512(d, s, n);
     else if (level == 1) stream_copy_avx2(d, s, n);
     else memcpy(d, s, n);

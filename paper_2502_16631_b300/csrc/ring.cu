@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <atomic>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -93,7 +94,9 @@ int ring_get(snap_set_s *s, Ring **out)
         return SNAP_ENOMEM;
     }
     const int hw = (int)std::thread::hardware_concurrency();
-    r->pool = new Pool(std::max(2, std::min(12, hw > 2 ? hw - 2 : 2)));
+    int nw = std::max(2, std::min(12, hw > 2 ? hw - 2 : 2));
+    if (const char *w = std::getenv("SNAP_RING_WORKERS")) nw = std::max(1, std::min(64, std::atoi(w)));
+    r->pool = new Pool(nw);
     s->ring = r;
     *out = r;
     return SNAP_OK;

@@ -101,7 +101,9 @@ static bool valid_cached(const snap_set_s *s, int mode, const TileShape &t)
     if (!one_of(t.stages, kStages)) return false;
     if (full ? !one_of(t.piece, kPieceGather) : !one_of(t.piece, kPieceHash)) return false;
     if (t.chains != 1 && !(t.chains == 2 && !full)) return false;
-    if (t.tma != 0 && !(t.tma == 1 && !full && t.chains == 1 && t.piece <= 128)) return false;
+    // the gather ignores the field (the tuner stores 1 for it); for the hash
+    // pass TMA staging needs one chain and pieces up to 128 bytes
+    if (t.tma != 0 && !(t.tma == 1 && (full || (t.chains == 1 && t.piece <= 128)))) return false;
     if (t.ctas != s->sms * ctas_per_sm(s)) return false;
     return tile_smem_bytes(t) <= kMaxSmem;
 }
