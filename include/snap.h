@@ -85,7 +85,9 @@ typedef struct {
     uint32_t stages;       /* staging buffers per warp; 0 = tuned default */
     uint64_t ring_bytes;   /* pinned ring for pageable images; default 4 GiB
                               (its host copy workers: min(12, host threads
-                              - 2), or $SNAP_RING_WORKERS) */
+                              - 2), or $SNAP_RING_WORKERS; a restore from a
+                              memory image fills slots with at most 8 of
+                              them, or $SNAP_RING_FILL_WORKERS) */
     uint32_t async_ctas;   /* CTAs of the background part of snap_checkpoint_async;
                               default 8 (enough to saturate the host link) */
     uint32_t hash_tma;     /* 1: stage the hash pass with 2D TMA tensor copies

@@ -39,7 +39,8 @@ struct Ring {
     int slots = 0;
     std::vector<cudaEvent_t> ev;   // one per slot: the end of the last kernel that used it
     std::vector<cudaEvent_t> ev0;  // one per slot: the start of that kernel (device timing)
-    Pool *pool = nullptr;
+    Pool *pool = nullptr;       // copy workers: checkpoint drains, file reads
+    Pool *fill_pool = nullptr;  // fewer workers for restore fills from memory images
     Job *d_jobs = nullptr;   // one job per slot (device)
     Job *h_jobs = nullptr;   // pinned staging
     unsigned long long *d_cursor = nullptr;  // one cursor per slot
@@ -51,6 +52,7 @@ void ring_free(snap_set_s *s)
     if (!r) return;
     if (s->st) cudaStreamSynchronize(s->st);
     delete r->pool;
+    delete r->fill_pool;
     for (auto e : r->ev) if (e) cudaEventDestroy(e);
     for (auto e : r->ev0) if (e) cudaEventDestroy(e);
     cudaFreeHost(r->host);
@@ -97,6 +99,15 @@ int ring_get(snap_set_s *s, Ring **out)
     int nw = std::max(2, std::min(12, hw > 2 ? hw - 2 : 2));
     if (const char *w = std::getenv("SNAP_RING_WORKERS")) nw = std::max(1, std::min(64, std::atoi(w)));
     r->pool = new Pool(nw);
+    // A restore's fills write the slots that the scatter kernel is reading
+    // over the link from host DRAM: fewer fill workers keep the fills just
+    // ahead of the link instead of bursting, and the kernel's reads of pinned
+    // memory slow down less (16 GiB through the 4 GiB ring on B300: scatter
+    // 49.4 GB/s with 12 fill workers, 51.4 with 8, 46.2 with 16; the
+    // checkpoint's drains are best with 12).
+    int nf = std::min(nw, 8);
+    if (const char *w = std::getenv("SNAP_RING_FILL_WORKERS")) nf = std::max(1, std::min(64, std::atoi(w)));
+    r->fill_pool = new Pool(nf);
     s->ring = r;
     *out = r;
     return SNAP_OK;
@@ -588,10 +599,11 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
     double kms = 0.0;
 
     // queue the fill of window w: it waits for the kernel of window w - slots
+    Pool *fills = io.mem ? r->fill_pool : r->pool;  // a file is read by the full pool
     auto queue_fill = [&](size_t w) {
         const int slot = (int)(w % r->slots);
         const uint64_t nbytes = win[w].b1 - win[w].b0;
-        const uint64_t np = parts_for(nbytes, r->pool->size());
+        const uint64_t np = parts_for(nbytes, fills->size());
         {
             std::lock_guard<std::mutex> lk(pg.mu);
             pg.left[w] = (int)np;
@@ -599,7 +611,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
         }
         for (uint64_t p = 0; p < np; ++p) {
             const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
-            r->pool->push([&, w, slot, p0, p1] {
+            fills->push([&, w, slot, p0, p1] {
                 if (w >= (size_t)r->slots && !pg.err) {
                     const size_t prev = w - r->slots;
                     if (!pg.wait(deadline, [&] { return pg.launched[prev] != 0; })) pg.err = SNAP_ETIMEDOUT;

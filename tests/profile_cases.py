@@ -9,6 +9,9 @@ under `ncu`; not collected by pytest).
     python tests/profile_cases.py ring [reps]     # 8 x 256 MiB, full checkpoints through the
                                                   # 4 GiB ring into a pageable image (32 gather
                                                   # launches of one 64 MiB window each)
+    python tests/profile_cases.py ringrestore [reps]  # the same state: one ring checkpoint, then
+                                                  # restores through the ring (32 scatter
+                                                  # launches each)
 """
 import os
 import sys
@@ -36,6 +39,18 @@ def main():
         img = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
         for _ in range(reps + 1):
             s.checkpoint(img, snap.FULL)
+    elif op == "ringrestore":
+        import numpy as np
+        ts = [torch.empty(256 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]
+        for t in ts:
+            t.random_(0, 256)
+        s = snap.Set(chunk_bytes=65536, ring_bytes=4096 * MiB)
+        for t in ts:
+            s.register(t)
+        img = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
+        used = s.checkpoint(img, snap.FULL)
+        for _ in range(reps + 1):
+            s.restore(img, used)
     elif op == "hash":
         x = torch.empty(1024 * MiB, dtype=torch.uint8, device="cuda")
         x.random_(0, 256)

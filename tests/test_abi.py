@@ -77,3 +77,15 @@ def test_host_only_calls_work_without_a_gpu():
     assert snap.lib().snap_host_register(None, 4096) == snap.EINVAL
     assert snap.lib().snap_host_register(ctypes.cast(buf, ctypes.c_void_p), 0) == snap.EINVAL
     assert snap.lib().snap_host_unregister(None) == snap.EINVAL
+    # the measurement probes check their arguments first too
+    v = ctypes.c_double()
+    L = snap.lib()
+    assert L.snap_host_copy_ceiling(0, 0, 1 << 30, 1, 0, ctypes.byref(v)) == snap.EINVAL   # no threads
+    assert L.snap_host_copy_ceiling(4, 3, 1 << 30, 1, 0, ctypes.byref(v)) == snap.EINVAL   # no direction 3
+    assert L.snap_host_copy_ceiling(1, 2, 1 << 30, 1, 0, ctypes.byref(v)) == snap.EINVAL   # both ways needs 2
+    assert L.snap_host_copy_ceiling(4, 0, 4096, 1, 0, ctypes.byref(v)) == snap.EINVAL      # under 1 MiB
+    assert L.snap_host_copy_ceiling(4, 0, 1 << 30, 0, 0, ctypes.byref(v)) == snap.EINVAL   # no rounds
+    assert L.snap_host_copy_ceiling(4, 0, 1 << 30, 1, 0, None) == snap.EINVAL
+    assert L.snap_link_ceiling(-1, 3, 1 << 20, 1, ctypes.byref(v)) == snap.EINVAL
+    t = snap.Tuning()
+    assert L.snap_get_tuning(None, 0, ctypes.byref(t)) == snap.EINVAL
