@@ -263,6 +263,17 @@ def traffic_ratio_from_profiles(kernel: str):
     return None
 
 
+def gather_traffic(state_bytes: int):
+    """DRAM bytes of one full-gather launch over `state_bytes`: the committed
+    per-launch figure for this kernel code, else its committed ratio times
+    the state bytes (one read per state byte), else None."""
+    t = traffic_from_profiles("snap_tiles_gather")
+    if t is None:
+        r = traffic_ratio_from_profiles("snap_tiles_gather")
+        t = None if r is None else int(r * state_bytes)
+    return t
+
+
 def traffic_from_profiles(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, valid
     only while the kernel source (its code, not its comments) is unchanged
@@ -273,9 +284,9 @@ def traffic_from_profiles(kernel: str):
         sha = kernel_source_key(src)
         for line in open(path):
             parts = line.split()
-            if len(parts) >= 4 and parts[0] == kernel and parts[3] == sha:
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] != "ratio" and parts[3] == sha:
                 return int(parts[2])
-    except OSError:
+    except (OSError, ValueError):
         pass
     return None
 
@@ -608,7 +619,7 @@ def measure_gpt2(args, rank, world, local, pg, steps, warmup, with_cpu):
         "roofline": {"bound": "host_link", "kernel": "snap_tiles (OP_GATHER, full checkpoint)",
                      "achieved": achieved, "peak": peaks["d2h"], "unit": "GB/s", "frac": achieved / peaks["d2h"],
                      "peak_source": "pinned cudaMemcpyAsync D2H, 1 GiB, best of 5, measured in this run",
-                     "traffic": traffic_from_profiles("snap_tiles_gather"),
+                     "traffic": gather_traffic(B),
                      "sm_path_peak": peaks["sm_d2h"], "frac_of_sm_path": achieved / peaks["sm_d2h"]},
         "roofline_restore": {"bound": "host_link", "kernel": "snap_tiles (OP_SCATTER)",
                              "achieved": B / (statistics.mean(per["scatter_kernel"]) * 1e-3) / 1e9,
