@@ -69,91 +69,6 @@ __global__ void k_shadow_copy(const AllocDesc *__restrict__ allocs, uint64_t n_a
     }
 }
 
-// ------------------------------------------------ dirty gather (pipelined)
-// One group's dirty chunks of a pipelined incremental checkpoint, copied from
-// the device into their patch slots in the mapped host image with plain
-// 16-byte loads and stores (eight in flight per lane, one warp per chunk).
-// It uses no shared memory and at most 64 registers, so its CTAs fit on the
-// SMs beside the hash kernel's CTAs (which hold the shared-memory CRC
-// tables): the hash pass keeps every SM while the link moves the dirty bytes.
-// The checks are the tile kernel's for OP_GATHER_DIRTY: the capacity flag,
-// the chunk inside its allocation, its dirty rank inside the allocation's
-// range of the list, 16-byte aligned addresses; a failed check records
-// ERR_BAD_TILE and the chunk is skipped.
-__device__ __forceinline__ void warp_zero_bytes(uint8_t *p, uint64_t n, int lane)
-{
-    uint64_t head = (16u - ((uintptr_t)p & 15u)) & 15u;
-    if (head > n) head = n;
-    if ((uint64_t)lane < head) p[lane] = 0;
-    p += head;
-    n -= head;
-    const uint64_t n16 = n >> 4;
-    for (uint64_t q = lane; q < n16; q += 32) reinterpret_cast<uint4 *>(p)[q] = make_uint4(0, 0, 0, 0);
-    const uint64_t rem = n & 15u;
-    if ((uint64_t)lane < rem) p[(n16 << 4) + lane] = 0;
-}
-
-__global__ void __launch_bounds__(128, 8) k_gather_dirty(const Job *__restrict__ job, Result *kres)
-{
-    const Job &jb = *job;
-    if (jb.cap_exceeded && *reinterpret_cast<volatile const unsigned long long *>(jb.cap_exceeded)) return;
-    const unsigned long long n = jb.n_tiles_dev ? *jb.n_tiles_dev : jb.n_tiles;
-    const unsigned long long toff = jb.tile_off_dev ? *jb.tile_off_dev : 0ull;
-    const uint64_t C = jb.chunk_bytes;
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t tt = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tt < n; tt += warps) {
-        const uint64_t chunk = jb.tile_list[tt + toff];
-        const uint64_t k = find_alloc_chunk(jb.allocs, jb.n_allocs, chunk);
-        const AllocDesc a = jb.allocs[k];
-        const uint64_t nk = (a.bytes + C - 1) / C;
-        const uint64_t i = chunk - a.chunk0;
-        const unsigned long long rank = jb.window_off + toff + tt;
-        bool bad = chunk < a.chunk0 || i >= nk || rank < jb.dstart[k] || rank >= jb.dstart[k + 1];
-        const uint64_t off = i * C;
-        const uint64_t L = bad ? 0 : ((a.bytes - off) < C ? (a.bytes - off) : C);
-        const uint8_t *src = reinterpret_cast<const uint8_t *>(a.ptr) + off;
-        uint8_t *dst = jb.host + jb.patch_data[k] + (rank - jb.dstart[k]) * C;
-        if (!bad) bad = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) != 0;
-        if (bad) {  // the same for every lane of the warp
-            if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
-            continue;
-        }
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-        const uint64_t nb = L >> 4;
-        constexpr uint32_t U = 8;
-        uint64_t q = lane;
-        for (; q + 32u * (U - 1) < nb; q += 32u * U) {
-            uint4 v[U];
-#pragma unroll
-            for (uint32_t u = 0; u < U; ++u) v[u] = s4[q + 32u * u];
-#pragma unroll
-            for (uint32_t u = 0; u < U; ++u) d4[q + 32u * u] = v[u];
-        }
-        for (; q < nb; q += 32u) d4[q] = s4[q];
-        const uint64_t rem = L & 15u;
-        if ((uint64_t)lane < rem) dst[(nb << 4) + lane] = src[(nb << 4) + lane];
-        if (L & 4095u) warp_zero_bytes(dst + L, upg(L) - L, lane);
-    }
-}
-
-cudaError_t launch_gather_dirty(const Job *job, Result *kres, int ctas, cudaStream_t st)
-{
-    k_gather_dirty<<<ctas, 128, 0, st>>>(job, kres);
-    return cudaGetLastError();
-}
-
-int gather_dirty_regs()
-{
-    cudaFuncAttributes at{};
-    if (cudaFuncGetAttributes(&at, k_gather_dirty) != cudaSuccess) {
-        cudaGetLastError();
-        return 255;
-    }
-    return at.numRegs;
-}
-
 cudaError_t launch_shadow_copy(const AllocDesc *allocs, uint64_t n_allocs, uint64_t C, uint64_t n_chunks,
                                uint8_t *shadow, int sms, cudaStream_t st)
 {

@@ -617,8 +617,7 @@ int async_ctas(const snap_set_s *s)
 // of the unpipelined sequence.  Used only when the image capacity covers the
 // largest possible patch, because a group's bytes are written before later
 // groups are laid out.
-static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const TileShape &shh, bool shared_sms,
-                                 GraphEntry **out)
+static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const TileShape &shh, GraphEntry **out)
 {
     const int H = s->n_pipe;
     for (cudaStream_t *p : {&s->st_pipe, &s->st_meta})
@@ -653,7 +652,6 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const Ti
     }
     TileShape shg = s->shape[SHAPE_GATHER];
     shg.ctas = kPipeGatherCtas;
-    const int plain_ctas = s->sms;  // shared_sms: one 4-warp CTA of the plain gather per SM
     const CombineConsts cch = make_combine_consts(s->C, shh.piece);
     const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
     const uint32_t *curp = s->d_hash[cur], *prevp = s->d_hash[1 - cur];
@@ -699,8 +697,7 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const Ti
             if (s->gal[g + 1] == s->gal[g]) continue;
             e = cudaStreamWaitEvent(q, s->ev_pipe[1 + H + g], 0);
             if (e == cudaSuccess)
-                e = shared_sms ? launch_gather_dirty(d->jobs + H + g, &d->res, plain_ctas, q)
-                               : launch_tiles(d->jobs + H + g, 1, &d->cursor[H + g], ccg, shg, &d->res, q);
+                e = launch_tiles(d->jobs + H + g, 1, &d->cursor[H + g], ccg, shg, &d->res, q);
         }
         // join the hash stream too (its last event precedes the last metadata,
         // but a join must name the stream's own last work)
@@ -708,31 +705,6 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const Ti
         if (e == cudaSuccess) e = enqueue_epilogue(s, q);
         return e;
     }, out);
-}
-
-// Whether a CTA of the plain dirty gather (128 threads, no shared memory,
-// at most 64 registers) fits on an SM beside one CTA of the hash kernel of
-// shape `sh`: then the hash launches of a pipelined incremental take every
-// SM and the gathers share them (the gathers need little but the link);
-// otherwise kPipeGatherCtas SMs are left to the tile kernel's gathers.  Only
-// the hash-only kernel (more than kMaxWarps warps, at most 64 registers a
-// thread by its launch bounds) leaves the registers for it.
-static bool gather_shares_sms(const snap_set_s *s, const TileShape &sh)
-{
-    if (std::getenv("SNAP_PIPE_RESERVED_SMS")) return false;  // the reserved-SM form, for measurements
-    if (sh.warps <= kMaxWarps || gather_dirty_regs() > 64) return false;
-    int smem_sm = 0, reserved = 0, threads_sm = 0, regs_sm = 0;
-    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, s->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, s->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, s->device) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    const size_t smem = tile_smem_bytes(sh) + (size_t)reserved;  // the hash CTA
-    const int threads = sh.warps * 32;
-    return smem + (size_t)reserved <= (size_t)smem_sm && threads + 128 <= threads_sm &&
-           64 * threads + 64 * 128 <= regs_sm;
 }
 
 // Fill the call block of a checkpoint into the mapped image `dimg` and get
@@ -766,10 +738,9 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
     }
     if (!from_shadow && s->n_groups >= 2 && cap >= s->patch_bound) {
         TileShape shp = shh;
-        const bool shared = gather_shares_sms(s, shh);
-        shp.ctas = shared ? s->sms : std::max(1, s->sms - kPipeGatherCtas);
+        shp.ctas = std::max(1, s->sms - kPipeGatherCtas);
         if (plan_pipeline(s, (uint64_t)shp.ctas * (uint64_t)shp.warps) >= 2)
-            return pipelined_incremental(s, cur, dimg, shp, shared, out);
+            return pipelined_incremental(s, cur, dimg, shp, out);
     }
     Job jh = base_job(s, OP_HASH);
     jh.allocs = allocs;

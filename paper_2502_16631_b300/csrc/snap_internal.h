@@ -167,13 +167,6 @@ cudaError_t launch_patch_meta(const AllocDesc *allocs, uint64_t n_allocs, uint64
                               const uint64_t *patch_data, const uint64_t *dstart,
                               const Result *res, const CallParams *cp, cudaStream_t st);
 
-// One group's dirty chunks (an OP_GATHER_DIRTY job with LAYOUT_IMAGE) copied
-// into their patch slots by a kernel with no shared memory and 128-thread
-// CTAs, small enough to share SMs with the hash kernel.  gather_dirty_regs:
-// its registers per thread (255 if unknown).
-cudaError_t launch_gather_dirty(const Job *job, Result *kres, int ctas, cudaStream_t st);
-int gather_dirty_regs();
-
 // Device-to-device copy of every allocation into the packed shadow buffer
 // (the cut of an asynchronous checkpoint).
 cudaError_t launch_shadow_copy(const AllocDesc *allocs, uint64_t n_allocs, uint64_t chunk_bytes, uint64_t n_chunks,
