@@ -605,7 +605,6 @@ __device__ void scatter_chunk(const uint8_t *src, uint8_t *dst, uint32_t L, int 
     if ((uint32_t)lane < rem) dst[(nb << 4) + lane] = src[(nb << 4) + lane];
 }
 
-// -------------------------------------------------------------- main kernel
 // Largest k with a[k].chunk0 <= chunk (ties: the largest index, so that
 // zero-byte allocations, which own no chunk, are never chosen).
 __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, uint64_t chunk)
@@ -618,6 +617,243 @@ __device__ __forceinline__ uint64_t find_alloc(const AllocDesc *a, uint64_t n, u
     return lo;
 }
 
+// ------------------------------------------ fused incremental: the roles
+// Wait (one thread) until *p >= v, bounded by kWaitNs; false if the wait
+// ran out (ERR_WAIT_TIMEOUT recorded) or another CTA recorded an error.
+__device__ bool fused_wait(const unsigned long long *p, unsigned long long v, Result *kres)
+{
+    const volatile unsigned long long *vp = p;
+    const volatile unsigned long long *verr = &kres->err;
+    if (*vp >= v) {
+        __threadfence();
+        return true;
+    }
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (*vp >= v) break;
+        if (*verr) return false;
+        if (global_ns() - t0 > kWaitNs) {
+            atomicOr(&kres->err, (unsigned long long)ERR_WAIT_TIMEOUT);
+            return false;
+        }
+        __nanosleep(200);
+    }
+    __threadfence();  // what the producer wrote before its release is visible
+    return true;
+}
+
+// Exclusive scan of one value per thread over the CTA (any multiple of 32
+// threads up to 1024); *total = the sum.  ws: 33 words of shared memory.
+__device__ unsigned long long cta_exscan(unsigned long long v, unsigned long long *total, unsigned long long *ws)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long t = lane < nw ? ws[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) ws[lane] = t;  // inclusive over warps
+        if (lane == nw - 1) ws[32] = t;
+    }
+    __syncthreads();
+    const unsigned long long r = (warp ? ws[warp - 1] : 0ull) + x - v;
+    *total = ws[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ uint64_t lower_bound_list(const uint32_t *a, uint64_t n, uint64_t key)
+{
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The group of a chunk: the last g with gch[g] <= chunk (an empty group
+// shares its start with the next one, which then owns the chunk).
+__device__ __forceinline__ int fused_group(const FusedIncr &f, uint64_t chunk)
+{
+    int lo = 0, hi = f.n_groups;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (f.gch[mid] <= chunk) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// The metadata role (one CTA): per group, in order, once its chunks are
+// hashed: the dirty list (ascending, continuing the running count), the
+// patch layout of its allocations (continuing the running offset; the
+// layout snap_format.h states), their records, hashes and dirty indices
+// written into the patch, then the group is released to the gather CTAs.
+__device__ void fused_meta(const Job &jb, FusedIncr &f, unsigned long long *ws, Result *kres)
+{
+    const uint64_t C = jb.chunk_bytes;
+    const uint32_t *cur = jb.hash_out;
+    unsigned long long run = 0;    // dirty entries listed so far
+    unsigned long long off = 64;   // patch offset of the next record
+    if (threadIdx.x == 0) kres->ts[TS_DIFF_END] = global_ns();  // the whole pipeline is copy time
+    for (int g = 0; g < f.n_groups; ++g) {
+        const uint64_t c0 = f.gch[g], c1 = f.gch[g + 1];
+        if (threadIdx.x == 0) ws[34] = fused_wait(&f.grp_done[g], c1 - c0, kres) ? 1ull : 0ull;
+        __syncthreads();
+        const bool ok = ws[34] != 0;
+        __syncthreads();
+        if (!ok) return;
+        if (g + 1 == f.n_groups && threadIdx.x == 0) kres->ts[TS_HASH_END] = global_ns();
+        // the group's dirty chunks, ascending
+        const unsigned long long beg = run;
+        for (uint64_t base = c0; base < c1; base += blockDim.x) {
+            const uint64_t c = base + threadIdx.x;
+            // other SMs wrote these hashes during this launch: read them at L2, never from a stale L1 line
+            const bool d = c < c1 && __ldcg(cur + c) != f.prev[c];
+            unsigned long long tot;
+            const unsigned long long ex = cta_exscan(d ? 1ull : 0ull, &tot, ws);
+            if (d) f.dlist[run + ex] = (uint32_t)c;
+            run += tot;
+        }
+        __syncthreads();  // the list is complete for every thread
+        // the layout of the group's allocations
+        const uint64_t a0 = f.gal[g], a1 = f.gal[g + 1];
+        for (uint64_t base = a0; base < a1; base += blockDim.x) {
+            const uint64_t k = base + threadIdx.x;
+            unsigned long long R = 0, meta_pad = 0, ds = 0;
+            if (k < a1) {
+                const AllocDesc a = jb.allocs[k];
+                const uint64_t nk = (a.bytes + C - 1) / C;
+                ds = lower_bound_list(f.dlist, run, a.chunk0);
+                const uint64_t de = lower_bound_list(f.dlist, run, a.chunk0 + nk);
+                const uint64_t nd = de - ds;
+                uint64_t data = nd * C;
+                if (nd && f.dlist[de - 1] == a.chunk0 + nk - 1) data = data - C + up_page(a.bytes - (nk - 1) * C);
+                const uint64_t meta = 32 + 4 * nk + 4 + 4 * nd;
+                meta_pad = (k == 0) ? up_page(64 + meta) - 64 : up_page(meta);
+                R = meta_pad + data;
+            }
+            unsigned long long tot;
+            const unsigned long long ex = cta_exscan(R, &tot, ws);
+            if (k < a1) {
+                f.patch_rec[k] = off + ex;
+                f.patch_data[k] = off + ex + meta_pad;
+                f.dstart[k] = ds;
+            }
+            off += tot;
+        }
+        if (threadIdx.x == 0) f.dstart[a1] = run;
+        __syncthreads();
+        // records, hashes, dirty indices and padding of the group's allocations
+        if (off <= f.cap)
+            for (uint64_t k = a0; k < a1; ++k) {
+                const AllocDesc a = jb.allocs[k];
+                const uint64_t nk = (a.bytes + C - 1) / C;
+                const uint64_t rec = f.patch_rec[k], data = f.patch_data[k];
+                const uint64_t ds = f.dstart[k], nd = f.dstart[k + 1] - ds;
+                uint64_t *r64 = reinterpret_cast<uint64_t *>(f.host + rec);
+                if (threadIdx.x == 0) {
+                    r64[0] = a.bytes;
+                    r64[1] = nk;
+                    r64[2] = data;
+                    r64[3] = 0;
+                }
+                uint32_t *h = reinterpret_cast<uint32_t *>(f.host + rec + 32);
+                for (uint64_t i = threadIdx.x; i < nk; i += blockDim.x) h[i] = __ldcg(cur + a.chunk0 + i);
+                if (threadIdx.x == 0) h[nk] = (uint32_t)nd;
+                for (uint64_t j = threadIdx.x; j < nd; j += blockDim.x) h[nk + 1 + j] = f.dlist[ds + j] - (uint32_t)a.chunk0;
+                const uint64_t zlo = rec + 36 + 4 * nk + 4 * nd;
+                uint32_t *z = reinterpret_cast<uint32_t *>(f.host + zlo);
+                const uint64_t nz = (data - zlo) / 4;
+                for (uint64_t q = threadIdx.x; q < nz; q += blockDim.x) z[q] = 0u;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            f.gbeg[g] = beg;
+            f.gcnt[g] = off <= f.cap ? run - beg : 0ull;  // over capacity: nothing is gathered
+            __threadfence();
+            atomicExch(&f.meta_ready[g], 1ull);
+        }
+    }
+    if (threadIdx.x == 0) {
+        kres->n_dirty = run;
+        kres->patch_bytes = off;
+        if (off > f.cap) kres->cap_exceeded = 1ull;
+    }
+}
+
+// The gather role: per group, in order, once its metadata is written, every
+// warp takes dirty chunks from the group's cursor and copies each into its
+// patch slot with 16-byte loads and stores (eight in flight per lane), then
+// zeroes the slot's padding.  The checks are the tile loop's for a dirty
+// gather: the chunk inside its allocation, its rank inside the allocation's
+// range of the list, 16-byte aligned addresses (else ERR_BAD_TILE, skipped).
+__device__ void fused_gather(const Job &jb, FusedIncr &f, Result *kres)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t C = jb.chunk_bytes;
+    for (int g = 0; g < f.n_groups; ++g) {
+        int ok = 1;
+        if (lane == 0) ok = fused_wait(&f.meta_ready[g], 1ull, kres) ? 1 : 0;
+        if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
+        const unsigned long long n = *reinterpret_cast<volatile unsigned long long *>(&f.gcnt[g]);
+        const unsigned long long beg = *reinterpret_cast<volatile unsigned long long *>(&f.gbeg[g]);
+        for (;;) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(&f.gcur[g], 1ull);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            if (t >= n) break;
+            // the list and the layout were written by the metadata CTA during
+            // this launch: read them at L2
+            const unsigned long long rank = beg + t;
+            const uint64_t chunk = __ldcg(f.dlist + rank);
+            const uint64_t k = find_alloc(jb.allocs, jb.n_allocs, chunk);
+            const AllocDesc a = jb.allocs[k];
+            const uint64_t nk = (a.bytes + C - 1) / C;
+            const uint64_t i = chunk - a.chunk0;
+            const uint64_t ds = __ldcg(reinterpret_cast<const unsigned long long *>(f.dstart) + k);
+            const uint64_t de = __ldcg(reinterpret_cast<const unsigned long long *>(f.dstart) + k + 1);
+            bool bad = chunk < a.chunk0 || i >= nk || rank < ds || rank >= de;
+            const uint64_t off = i * C;
+            const uint64_t L = bad ? 0 : ((a.bytes - off) < C ? (a.bytes - off) : C);
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(a.ptr) + off;
+            uint8_t *dst = f.host + __ldcg(reinterpret_cast<const unsigned long long *>(f.patch_data) + k) + (rank - ds) * C;
+            if (!bad) bad = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) != 0;
+            if (bad) {  // the same for every lane
+                if (lane == 0) atomicOr(&kres->err, (unsigned long long)ERR_BAD_TILE);
+                continue;
+            }
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            const uint64_t nb = L >> 4;
+            constexpr uint32_t U = 8;
+            uint64_t q = (uint64_t)lane;
+            for (; q + 32u * (U - 1) < nb; q += 32u * U) {
+                uint4 v[U];
+#pragma unroll
+                for (uint32_t u = 0; u < U; ++u) v[u] = s4[q + 32u * u];
+#pragma unroll
+                for (uint32_t u = 0; u < U; ++u) d4[q + 32u * u] = v[u];
+            }
+            for (; q < nb; q += 32u) d4[q] = s4[q];
+            const uint64_t rem = L & 15u;
+            if ((uint64_t)lane < rem) dst[(nb << 4) + lane] = src[(nb << 4) + lane];
+            if (L & 4095u) warp_zero(dst + L, up_page(L) - L, lane);
+        }
+    }
+}
+
+// -------------------------------------------------------------- main kernel
 // HASH_ONLY instantiation: only OP_HASH / OP_VERIFY jobs, up to 32 warps per
 // CTA (1024 threads, so at most 64 registers a thread) to keep more lookup
 // chains in flight; the general one serves every op with up to 16 warps.
@@ -641,6 +877,17 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
     uint8_t *stage_all = smem + kTableBytes;
     uint64_t *mbars = reinterpret_cast<uint64_t *>(stage_all + (size_t)warps * stages * stage_bytes);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(mbars + warps * stages);
+
+    // a fused incremental checkpoint's metadata CTA and gather CTAs (the CTA
+    // index decides the role of the whole CTA)
+    if (n_jobs == 1 && jobs[0].fused && (int)blockIdx.x >= jobs[0].fused->n_hash_ctas) {
+        FusedIncr &f = *jobs[0].fused;
+        if ((int)blockIdx.x == f.n_hash_ctas)
+            fused_meta(jobs[0], f, reinterpret_cast<unsigned long long *>(stage_all), kres);
+        else
+            fused_gather(jobs[0], f, kres);
+        return;
+    }
 
     // the lookups assume the tables at kTableBase; the condition is the same
     // for every thread, so the whole CTA leaves together
@@ -761,6 +1008,10 @@ snap_tiles(const Job *__restrict__ jobs, int n_jobs, int n_jobs_a, unsigned long
                     atomicAdd(&jb.res->mismatches, 1ull);
                     atomicMin(&jb.res->first_bad, (unsigned long long)chunk);
                 }
+                if (jb.fused) {  // release the hash to the metadata CTA
+                    __threadfence();
+                    atomicAdd(&jb.fused->grp_done[fused_group(*jb.fused, chunk)], 1ull);
+                }
             }
             break;
         case OP_GATHER:
@@ -856,6 +1107,54 @@ cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigne
         snap_tiles<false><<<sh.ctas, sh.warps * 32, smem, st>>>(jobs_dev, n_jobs, n_jobs_a, cursor_a, cursor_b, cc,
                                                                 sh.stages, sh.piece, sh.chains, sh.tma, kres);
     return cudaGetLastError();
+}
+
+cudaError_t launch_fused_incr(const Job *job_dev, unsigned long long *cursor, const CombineConsts &cc,
+                              const TileShape &sh, int grid, Result *kres, cudaStream_t st)
+{
+    const size_t smem = tile_smem_bytes(sh);
+    if (smem > kMaxSmem || sh.warps < 1 || sh.warps > kMaxHashWarps || grid < 3) return cudaErrorInvalidValue;
+    if (sh.chains < 1 || sh.chains > 2 || sh.stages < 1 || sh.piece < 32 || sh.piece > 256 || (sh.piece & 15))
+        return cudaErrorInvalidValue;
+    // the metadata CTA's scan words live in the staging area
+    if ((size_t)sh.warps * sh.stages * 32 * sh.chains * sh.piece < 35 * sizeof(unsigned long long))
+        return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)sh.warps * 32u);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at{};
+    at.id = cudaLaunchAttributeCooperative;  // every CTA resident: the roles wait on one another
+    at.val.cooperative = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    unsigned long long *none = nullptr;
+    if (sh.warps > kMaxWarps)
+        return cudaLaunchKernelEx(&cfg, snap_tiles<true>, job_dev, 1, 1, cursor, none, cc, sh.stages, sh.piece,
+                                  sh.chains, sh.tma, kres);
+    return cudaLaunchKernelEx(&cfg, snap_tiles<false>, job_dev, 1, 1, cursor, none, cc, sh.stages, sh.piece, sh.chains,
+                              sh.tma, kres);
+}
+
+bool fused_incr_fits(const TileShape &sh, int grid, int device)
+{
+    int coop = 0, sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t smem = tile_smem_bytes(sh);
+    const cudaError_t e =
+        sh.warps > kMaxWarps
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, snap_tiles<true>, sh.warps * 32, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, snap_tiles<false>, sh.warps * 32, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return coop != 0 && (long)per * sms >= grid;
 }
 
 cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor, const CombineConsts &cc,

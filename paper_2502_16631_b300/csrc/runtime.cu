@@ -707,6 +707,71 @@ static int pipelined_incremental(snap_set_s *s, int cur, uint8_t *dimg, const Ti
     }, out);
 }
 
+// The fused incremental checkpoint (one cooperative launch whose CTAs hash,
+// lay out and gather group by group; see FusedIncr).  Groups are runs of
+// whole allocations of about equal bytes (at least max(64 MiB, 1024 chunks)
+// each, at most kFusedMaxGroups): unlike the launch-per-stage pipeline there
+// is no launch boundary to align with the hash waves, so the groups can be
+// finer, and the hash CTAs never stop between them.  Fills the group table
+// of `f`; returns the group count (below 2: the state is too small).
+static int plan_fused(const snap_set_s *s, FusedIncr &f)
+{
+    const uint64_t min_group = std::max<uint64_t>(64ull << 20, 1024 * s->C);
+    const uint64_t G = std::min<uint64_t>((uint64_t)kFusedMaxGroups, s->total_bytes / min_group);
+    if (G < 2) return 0;
+    const uint64_t per = (s->total_bytes + G - 1) / G;
+    int g = 0;
+    uint64_t acc = 0;
+    f.gal[0] = 0;
+    f.gch[0] = 0;
+    for (size_t k = 0; k < s->desc.size(); ++k) {
+        acc += s->desc[k].bytes;
+        if (acc >= (uint64_t)(g + 1) * per && (uint64_t)(g + 1) < G && k + 1 < s->desc.size()) {
+            ++g;  // group g - 1 ends after allocation k
+            f.gal[g] = k + 1;
+            f.gch[g] = s->desc[k + 1].chunk0;
+        }
+    }
+    f.gal[g + 1] = s->desc.size();
+    f.gch[g + 1] = s->n_chunks;
+    f.n_groups = g + 1;
+    return f.n_groups;
+}
+
+static bool fused_ok(snap_set_s *s, const TileShape &shh, FusedIncr &f)
+{
+    if (std::getenv("SNAP_FUSED_OFF")) return false;  // the launch-per-stage pipeline, for measurements
+    if (s->sms - 1 - kPipeGatherCtas < 1 || plan_fused(s, f) < 2) return false;
+    return fused_incr_fits(shh, s->sms, s->device);
+}
+
+static int fused_incremental(snap_set_s *s, int cur, uint8_t *dimg, uint64_t cap, const TileShape &shh,
+                             GraphEntry **out)
+{
+    CallBlock &cb = *s->h_cb;  // the counters were zeroed by reset_call; plan_fused filled the groups
+    FusedIncr &f = cb.fused;
+    f.prev = s->d_hash[1 - cur];
+    f.dlist = s->d_dlist;
+    f.patch_rec = s->d_patch_rec;
+    f.patch_data = s->d_patch_data;
+    f.dstart = s->d_dstart;
+    f.host = dimg;
+    f.cap = cap;
+    f.n_hash_ctas = s->sms - 1 - kPipeGatherCtas;  // one metadata CTA, kPipeGatherCtas gather CTAs
+    Job jh = base_job(s, OP_HASH);
+    jh.hash_out = s->d_hash[cur];
+    jh.fused = &s->d_cb->fused;
+    cb.jobs[0] = jh;
+    const CombineConsts cch = make_combine_consts(s->C, shh.piece);
+    CallBlock *d = s->d_cb;
+    return get_graph(s, GK_INCR_FUSED, cur, [&](cudaStream_t q) {
+        cudaError_t e = enqueue_prologue(s, q);
+        if (e == cudaSuccess) e = launch_fused_incr(d->jobs, &d->cursor[0], cch, shh, s->sms, &d->res, q);
+        if (e == cudaSuccess) e = enqueue_epilogue(s, q);
+        return e;
+    }, out);
+}
+
 // Fill the call block of a checkpoint into the mapped image `dimg` and get
 // (capturing it on first use) its graph: FULL = records + gather of every
 // chunk with its CRC; INCREMENTAL = hash, diff against the committed table,
@@ -737,6 +802,7 @@ int checkpoint_graph(snap_set_s *s, int mode, int cur, uint8_t *dimg, uint64_t c
         }, out);
     }
     if (!from_shadow && s->n_groups >= 2 && cap >= s->patch_bound) {
+        if (fused_ok(s, shh, s->h_cb->fused)) return fused_incremental(s, cur, dimg, cap, shh, out);
         TileShape shp = shh;
         shp.ctas = std::max(1, s->sms - kPipeGatherCtas);
         if (plan_pipeline(s, (uint64_t)shp.ctas * (uint64_t)shp.warps) >= 2)

@@ -35,13 +35,15 @@ struct CallBlock {
     unsigned long long gbeg[kMaxPipe];             // pipelined incremental: each group's
     unsigned long long gcnt[kMaxPipe];             //   dirty-list range
     unsigned long long run_off;                     //   and the running patch offset
+    FusedIncr fused;                                // fused incremental: groups and counters
     Result res;
     CallParams cp;
     Job jobs[kMaxJobs];
 };
 
 enum EventId { EV_BEGIN = 0, EV_HASH_END, EV_DIFF_END, EV_COPY_END, EV_END, EV_COUNT };
-enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY, GK_ASYNC_FULL, GK_ASYNC_INCR, GK_INCR_PIPE };
+enum GraphKind { GK_FULL = 0, GK_INCR, GK_RESTORE, GK_VERIFY, GK_ASYNC_FULL, GK_ASYNC_INCR, GK_INCR_PIPE,
+                 GK_INCR_FUSED };
 enum ShapeKind { SHAPE_GATHER = 0, SHAPE_HASH, SHAPE_SCATTER, SHAPE_COUNT };
 
 struct GraphEntry {

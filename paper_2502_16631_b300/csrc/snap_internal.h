@@ -63,6 +63,8 @@ enum ResultErr : unsigned long long {
     ERR_SMEM_BASE = 4ull,      // dynamic shared memory not where the CRC lookups expect it
 };
 
+struct FusedIncr;
+
 // One job: a set of chunk tiles with one operation.
 struct Job {
     const AllocDesc *allocs;
@@ -86,6 +88,35 @@ struct Job {
     uint64_t test_stall;           // test hook, 0 in every normal call: the warp that takes
                                    // tile test_stall - 1 waits on a stage no copy fills, so
                                    // its bounded wait runs out (ERR_WAIT_TIMEOUT)
+    FusedIncr *fused;              // OP_HASH of a fused incremental checkpoint, else null
+};
+
+// A fused incremental checkpoint: one cooperative launch of the tile kernel
+// whose CTAs take three roles.  CTAs [0, n_hash_ctas) hash every chunk in
+// ascending order (the job's tiles) and count each completed chunk against
+// its group; CTA n_hash_ctas waits for each group in turn and diffs it
+// (ascending dirty list), lays out its allocations' patch records and
+// writes their metadata into the patch; the remaining CTAs wait for each
+// group's metadata and copy its dirty chunks into their patch slots.  A
+// group is a run of whole allocations, chunks [gch[g], gch[g+1]) and
+// allocations [gal[g], gal[g+1]).  Every wait is bounded (ERR_WAIT_TIMEOUT);
+// the cooperative launch keeps every CTA resident, so no role waits on a CTA
+// that is not running.
+constexpr int kFusedMaxGroups = 64;
+struct FusedIncr {
+    const uint32_t *prev;      // committed hashes
+    uint32_t *dlist;           // ascending dirty chunk list
+    uint64_t *patch_rec, *patch_data, *dstart;
+    uint8_t *host;             // device-visible address of the patch image
+    uint64_t cap;              // its capacity
+    int n_groups, n_hash_ctas;
+    uint64_t gch[kFusedMaxGroups + 1];
+    uint64_t gal[kFusedMaxGroups + 1];
+    // counters and results, zero at the start of every call
+    unsigned long long grp_done[kFusedMaxGroups];    // chunks hashed per group
+    unsigned long long meta_ready[kFusedMaxGroups];  // 1 once a group's metadata is written
+    unsigned long long gcur[kFusedMaxGroups];        // gather cursor per group
+    unsigned long long gbeg[kFusedMaxGroups], gcnt[kFusedMaxGroups];  // its dirty-list range
 };
 
 constexpr int kMaxJobs = 64;
@@ -131,6 +162,14 @@ constexpr size_t kMaxSmem = 232448;  // 227 KiB opt-in per CTA
 cudaError_t launch_tiles(const Job *jobs_dev, int n_jobs, unsigned long long *cursor,
                          const CombineConsts &cc, const TileShape &sh, Result *kres,
                          cudaStream_t st, bool overlap_prev = false);
+// The fused incremental checkpoint: one cooperative launch of `grid` CTAs
+// of shape `sh` (hash-role CTAs = fused->n_hash_ctas of them), job = its
+// OP_HASH job (with `fused` set).  fused_incr_fits: whether the device can
+// keep `grid` CTAs of that shape resident at once.
+cudaError_t launch_fused_incr(const Job *job_dev, unsigned long long *cursor, const CombineConsts &cc,
+                              const TileShape &sh, int grid, Result *kres, cudaStream_t st);
+bool fused_incr_fits(const TileShape &sh, int grid, int device);
+
 // Two job groups with their own cursors: jobs [0, n_jobs_a) (device to
 // host) and [n_jobs_a, n_jobs) (host to device), worked on concurrently.
 cudaError_t launch_tiles2(const Job *jobs_dev, int n_jobs, int n_jobs_a, unsigned long long *cursor_a,
