@@ -691,12 +691,17 @@ def _pipeline_state(seed):
     return sizes, ts
 
 
+@pytest.mark.parametrize("form", ["fused", "stages"])
 @pytest.mark.parametrize("C", [65536, 16384])
-def test_pipelined_incremental_matches_oracle_and_the_serial_form(C):
+def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monkeypatch):
     """Large enough for several allocation groups: the pipelined patch (image
     capacity covers the largest patch) and the serial one (capacity one byte
     short of that bound) both equal the oracle's patch, byte for byte, at 0 %,
-    a few and 100 % dirty chunks."""
+    a few and 100 % dirty chunks.  Both pipelined forms: the fused one (one
+    cooperative launch whose CTAs hash, lay out and gather group by group,
+    the default) and the launch-per-stage one (SNAP_FUSED_OFF)."""
+    if form == "stages":
+        monkeypatch.setenv("SNAP_FUSED_OFF", "1")
     sizes, ts = _pipeline_state(31)
     a = make_set(ts, C)
     b = make_set(ts, C)
@@ -730,7 +735,10 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C):
         assert used_a == exp.size and np.array_equal(pa.view(used_a), exp), name
         assert used_b == exp.size and np.array_equal(pb.view(used_b), exp), name
         assert st_a["dirty_chunks"] == st_b["dirty_chunks"] == nd
-        assert st_a["kernel_launches"] > st_b["kernel_launches"]  # the group-wise sequence ran
+        if form == "fused":  # one fused launch between the two phase stamps
+            assert st_a["kernel_launches"] == 3
+        else:  # the launch-per-stage sequence ran
+            assert st_a["kernel_launches"] > st_b["kernel_launches"]
         prev = [oracle.chunk_hashes(h, C) for h in cur]
         gen += 1
     a.close()
