@@ -525,9 +525,9 @@ static void reset_call(snap_set_s *s, uint8_t *image, uint64_t cap)
 }
 
 // Test hook: SNAP_TEST_STALL_TILE=<n> (unset in normal use) makes the warp
-// that takes tile n of a direct full checkpoint's gather or of a verify wait
-// on a stage that no copy fills, so that the kernel's bounded wait runs out
-// and its error path runs.
+// that takes tile n of a direct full checkpoint's gather, of a verify or of
+// a fused incremental's hash wait on a stage that no copy fills, so that the
+// kernel's bounded wait runs out and its error path runs.
 static uint64_t test_stall_tile()
 {
     const char *e = std::getenv("SNAP_TEST_STALL_TILE");
@@ -761,6 +761,7 @@ static int fused_incremental(snap_set_s *s, int cur, uint8_t *dimg, uint64_t cap
     Job jh = base_job(s, OP_HASH);
     jh.hash_out = s->d_hash[cur];
     jh.fused = &s->d_cb->fused;
+    jh.test_stall = test_stall_tile();  // the give-up test hook reaches the fused hash too
     cb.jobs[0] = jh;
     const CombineConsts cch = make_combine_consts(s->C, shh.piece);
     CallBlock *d = s->d_cb;

@@ -745,6 +745,43 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
     b.close()
 
 
+def test_fused_incremental_gives_up_and_the_set_recovers(monkeypatch):
+    """The fused incremental's device-side waits reach their error path
+    without a fault: with the test hook SNAP_TEST_STALL_TILE one hash warp's
+    bounded wait runs out; the metadata CTA waiting for that warp's group and
+    the gather CTAs waiting for its metadata see the recorded error (or run
+    out themselves) and leave; the call returns SNAP_ECUDA inside the call
+    deadline with nothing committed, and the next incremental (fused again)
+    equals the oracle's patch."""
+    import time
+    C = 65536
+    sizes, ts = _pipeline_state(41)
+    s = make_set(ts, C)
+    full = snap.HostBuffer(s.image_bytes(snap.FULL))
+    patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+    s.checkpoint(full, snap.FULL)
+    prev = [oracle.chunk_hashes(h, C) for h in readback(ts)]
+    nch = [(n + C - 1) // C for n in sizes]
+    base, gen = s.committed_hashes(sum(nch))
+    base = base.copy()
+    mutate(ts, C, [(k, 0) for k, n in enumerate(nch) if n], seed=42)
+    cur = readback(ts)
+    monkeypatch.setenv("SNAP_TEST_STALL_TILE", "100")
+    t0 = time.perf_counter()
+    rc, _ = s.checkpoint_status(patch, snap.INCREMENTAL)
+    dt = time.perf_counter() - t0
+    assert rc == snap.ECUDA and s.stats()["device_errors"] & 1
+    assert dt < 9.0  # the stalled warp's two bounded waits; the call deadline is 10 s
+    h2, g2 = s.committed_hashes(sum(nch))
+    assert g2 == gen and np.array_equal(h2, base)
+    monkeypatch.delenv("SNAP_TEST_STALL_TILE")
+    used = s.checkpoint(patch, snap.INCREMENTAL)
+    assert s.stats()["kernel_launches"] == 3 and s.stats()["device_errors"] == 0  # the fused form, clean
+    rc, exp, nd = oracle.write_patch(cur, C, prev, 1, 0)
+    assert rc == 0 and used == exp.size and np.array_equal(patch.view(used), exp)
+    s.close()
+
+
 def test_gpt2_state_pipelined_incremental_parity():
     """GPT-2-small training state (2.26 GB, eight allocation groups): a 10 %
     clustered mutation; the pipelined patch equals the oracle's, and the
