@@ -754,29 +754,27 @@ __device__ void fused_meta(const Job &jb, FusedIncr &f, unsigned long long *ws, 
         }
         if (threadIdx.x == 0) f.dstart[a1] = run;
         __syncthreads();
-        // records, hashes, dirty indices and padding of the group's allocations
-        if (off <= f.cap)
-            for (uint64_t k = a0; k < a1; ++k) {
+        // records, hashes, dirty indices and padding of the group's
+        // allocations, one warp per allocation
+        if (off <= f.cap) {
+            const unsigned lane = threadIdx.x & 31u, nwarps = blockDim.x >> 5;
+            for (uint64_t k = a0 + (threadIdx.x >> 5); k < a1; k += nwarps) {
                 const AllocDesc a = jb.allocs[k];
                 const uint64_t nk = (a.bytes + C - 1) / C;
                 const uint64_t rec = f.patch_rec[k], data = f.patch_data[k];
                 const uint64_t ds = f.dstart[k], nd = f.dstart[k + 1] - ds;
                 uint64_t *r64 = reinterpret_cast<uint64_t *>(f.host + rec);
-                if (threadIdx.x == 0) {
-                    r64[0] = a.bytes;
-                    r64[1] = nk;
-                    r64[2] = data;
-                    r64[3] = 0;
-                }
+                if (lane < 4) r64[lane] = lane == 0 ? a.bytes : lane == 1 ? nk : lane == 2 ? data : 0ull;
                 uint32_t *h = reinterpret_cast<uint32_t *>(f.host + rec + 32);
-                for (uint64_t i = threadIdx.x; i < nk; i += blockDim.x) h[i] = __ldcg(cur + a.chunk0 + i);
-                if (threadIdx.x == 0) h[nk] = (uint32_t)nd;
-                for (uint64_t j = threadIdx.x; j < nd; j += blockDim.x) h[nk + 1 + j] = f.dlist[ds + j] - (uint32_t)a.chunk0;
+                for (uint64_t i = lane; i < nk; i += 32) h[i] = __ldcg(cur + a.chunk0 + i);
+                if (lane == 0) h[nk] = (uint32_t)nd;
+                for (uint64_t j = lane; j < nd; j += 32) h[nk + 1 + j] = f.dlist[ds + j] - (uint32_t)a.chunk0;
                 const uint64_t zlo = rec + 36 + 4 * nk + 4 * nd;
                 uint32_t *z = reinterpret_cast<uint32_t *>(f.host + zlo);
                 const uint64_t nz = (data - zlo) / 4;
-                for (uint64_t q = threadIdx.x; q < nz; q += blockDim.x) z[q] = 0u;
+                for (uint64_t q = lane; q < nz; q += 32) z[q] = 0u;
             }
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             f.gbeg[g] = beg;
