@@ -1274,7 +1274,8 @@ def run_serving(args, rank, world, local, pg):
               "check": "per completed request (every run), two chunks: the tenant's device bytes == the image's "
                        "(or the patch's dirty-chunk) bytes, and the oracle's CRC-32C of them == the stored hash"}
     both = link_peak_both(torch)
-    workers = min(32, max(2, os.cpu_count() or 2))  # the server's copy workers (one per host thread)
+    workers = int(os.environ.get("SNAP_WORKERS", "0")) or min(40, max(2, ((os.cpu_count() or 2) * 5 + 3) // 4))
+    # (the server's copy workers: 5 per 4 host threads unless SNAP_WORKERS says otherwise)
     hc = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3)
     hc_link = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3, with_link=True)
     # a staged byte costs host DRAM a read and a write for the copy plus one

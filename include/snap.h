@@ -398,8 +398,8 @@ SNAP_API int snap_get_tuning(snap_set s, int mode, snap_tuning *out);
  * batched into shared persistent launches (continuous batching), so requests
  * that arrive while others run overlap on the device.  The server pins a
  * staging pool of o->ring_bytes (else $SNAP_SERVER_POOL_BYTES, else 8 GiB;
- * at most pinned_budget) in slots of up to 64 MiB, and runs one host copy
- * worker per host thread ($SNAP_WORKERS overrides) to move window data
+ * at most pinned_budget) in slots of up to 64 MiB, and runs 5 host copy
+ * workers per 4 host threads ($SNAP_WORKERS overrides) to move window data
  * between the pool and the tenants' images.  o may be NULL (chunk_bytes,
  * timeout_ms and device as for snap_set_create).  Errors: EINVAL (zero
  * budget, bad chunk size), ENOMEM (pool), ECUDA. */

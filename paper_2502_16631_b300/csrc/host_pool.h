@@ -1,7 +1,11 @@
 // A fixed pool of host worker threads running queued tasks in FIFO order
 // (ring and server copies between pinned slots and pageable images).
 #pragma once
+#include <pthread.h>
+#include <sched.h>
+
 #include <condition_variable>
+#include <cstdlib>
 #include <deque>
 #include <functional>
 #include <mutex>
@@ -14,7 +18,19 @@ class Pool {
 public:
     explicit Pool(int n)
     {
-        for (int i = 0; i < n; ++i) th_.emplace_back([this] { run(); });
+        // SNAP_PIN_WORKERS=1 pins worker i to host CPU i modulo the CPU count
+        // (for measurements; by default the scheduler places them)
+        const char *pin = std::getenv("SNAP_PIN_WORKERS");
+        const int ncpu = (int)std::thread::hardware_concurrency();
+        for (int i = 0; i < n; ++i) {
+            th_.emplace_back([this] { run(); });
+            if (pin && pin[0] == '1' && ncpu > 0) {
+                cpu_set_t set;
+                CPU_ZERO(&set);
+                CPU_SET(i % ncpu, &set);
+                pthread_setaffinity_np(th_.back().native_handle(), sizeof set, &set);
+            }
+        }
     }
     ~Pool()
     {

@@ -778,10 +778,14 @@ int snap_server_create(snap_server *out, uint64_t pinned_budget, uint64_t hbm_bu
         return e == cudaErrorMemoryAllocation ? SNAP_ENOMEM : SNAP_ECUDA;
     }
     for (int i = 0; i < sv->nslots; ++i) sv->free_slots.push_back(i);
-    // copy workers: one per host thread (the copies are memory-bound; on a
-    // 16-thread host 16 workers moved 7 % more than 12 and cut p50 by 16 %)
+    // copy workers: 5 per 4 host threads (the copies are memory-bound and a
+    // worker waits on its window now and then; on a 16-thread host, 32
+    // tenants at 20 requests/s: 20 workers moved 54.3-54.7 GB/s of link
+    // traffic with p50 2.2-2.5 s over four runs, 16 workers 46.8-53.5 GB/s
+    // with p50 2.8-10.6 s, 24 workers 53.5-53.9 GB/s; earlier 16 workers had
+    // moved 7 % more than 12)
     const int hw = (int)std::thread::hardware_concurrency();
-    int nw = std::max(2, std::min(32, hw));
+    int nw = std::max(2, std::min(40, (hw * 5 + 3) / 4));
     if (const char *w = std::getenv("SNAP_WORKERS")) nw = std::max(1, std::min(64, std::atoi(w)));
     sv->workers = new Pool(nw);
     sv->sched = std::thread(scheduler, sv);
