@@ -1275,9 +1275,12 @@ def run_serving(args, rank, world, local, pg):
                        "(or the patch's dirty-chunk) bytes, and the oracle's CRC-32C of them == the stored hash"}
     both = link_peak_both(torch)
     workers = int(os.environ.get("SNAP_WORKERS", "0")) or min(40, max(2, ((os.cpu_count() or 2) * 5 + 3) // 4))
-    # (the server's copy workers: 5 per 4 host threads unless SNAP_WORKERS says otherwise)
-    hc = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3)
-    hc_link = snap.host_copy_ceiling(workers, 2, 2 * GiB, 3, with_link=True)
+    # (the server's copy workers: 5 per 4 host threads unless SNAP_WORKERS says otherwise).  The copy
+    # ceiling is probed with one thread per host CPU: the probe times its slowest thread, and more threads
+    # than CPUs make that a preempted thread's time, not the memory's
+    probe_threads = max(2, min(workers, os.cpu_count() or 2))
+    hc = snap.host_copy_ceiling(probe_threads, 2, 2 * GiB, 3)
+    hc_link = snap.host_copy_ceiling(probe_threads, 2, 2 * GiB, 3, with_link=True)
     # a staged byte costs host DRAM a read and a write for the copy plus one
     # access for the link transfer; the copy probe moves 2 DRAM bytes per byte
     host_bound = 2.0 * hc / 3.0
@@ -1321,7 +1324,8 @@ def run_serving(args, rank, world, local, pg):
                               "achieved": link_gbs, "peak": peak, "unit": "GB/s", "frac": link_gbs / peak,
                               "link_peak_both": both["sm_both"], "ce_both": both["ce_both"],
                               "host_copy_gbs": hc, "host_copy_gbs_under_link_load": hc_link,
-                              "host_memory_bound": host_bound, "copy_workers": workers, "offered": offered_gbs,
+                              "host_memory_bound": host_bound, "copy_workers": workers,
+                              "probe_threads": probe_threads, "offered": offered_gbs,
                               "note": "achieved = image, patch and restore bytes over the link / wall time; peak = "
                                       "min(SM loads/stores in both directions at once (snap_link_ceiling 2), "
                                       "2/3 x the workers' pinned<->pageable copy rate (snap_host_copy_ceiling 2): "
