@@ -12,6 +12,10 @@ under `ncu`; not collected by pytest).
     python tests/profile_cases.py ringrestore [reps]  # the same state: one ring checkpoint, then
                                                   # restores through the ring (32 scatter
                                                   # launches each)
+    python tests/profile_cases.py fused [reps]    # 8 x 256 MiB, one full checkpoint, then fused
+                                                  # incremental checkpoints with 10 % of the
+                                                  # chunks changed before each (one cooperative
+                                                  # launch each)
 """
 import os
 import sys
@@ -39,6 +43,22 @@ def main():
         img = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
         for _ in range(reps + 1):
             s.checkpoint(img, snap.FULL)
+    elif op == "fused":
+        ts = [torch.empty(256 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]
+        for t in ts:
+            t.random_(0, 256)
+        s = snap.Set(chunk_bytes=65536)
+        for t in ts:
+            s.register(t)
+        full = snap.HostBuffer(s.image_bytes(snap.FULL))
+        patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
+        s.checkpoint(full, snap.FULL)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        for _ in range(reps):
+            for t in ts:  # every tenth 64 KiB chunk changes
+                t.view(-1, 65536)[::10] ^= 0x5A
+            s.checkpoint(patch, snap.INCREMENTAL)
     elif op == "ringrestore":
         import numpy as np
         ts = [torch.empty(256 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]

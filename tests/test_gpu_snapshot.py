@@ -554,6 +554,21 @@ def test_device_wait_gives_up_and_the_set_recovers(monkeypatch):
     s.close()
 
 
+def test_measurement_probes_report_rates():
+    """The two measurement probes the bench reports its ceilings from: the
+    SM-path link rate in each direction and both at once, and the host copy
+    rate between pinned and pageable memory in each direction, both at once,
+    and under link load -- each a positive rate below anything physical."""
+    for d in (0, 1, 2):
+        v = snap.link_ceiling(d, 64 << 20, 2)
+        assert 1.0 < v < 500.0, (d, v)
+    for d, th in ((0, 2), (1, 2), (2, 4)):
+        v = snap.host_copy_ceiling(th, d, 64 << 20, 2)
+        assert 0.1 < v < 2000.0, (d, v)
+    v = snap.host_copy_ceiling(4, 2, 64 << 20, 1, with_link=True)
+    assert 0.1 < v < 2000.0
+
+
 def test_stats_report_phases():
     ts, _ = device_state([64 * 65536], seed=32)
     s = make_set(ts, 65536)
