@@ -1057,6 +1057,10 @@ def run_llama7b(args, rank, world, local, pg):
                         "-> return); the step itself moves the state to and from pageable host memory, so this "
                         "equals value up to the host's call overhead"},
         "image_populate_s": populate_s,
+        "memory": {"host_image_bytes": nimg, "host_pinned_ring_bytes": 2 * 4 * GiB,
+                   "device_state_bytes": 2 * B,
+                   "note": "one pageable image of the whole state; a 4 GiB pinned ring per buffer set; two "
+                           "resident buffer sets on the device (the checkpointed one and the restore target)"},
         "gpu_launches": counts["kernels"],
         "clocks": clk,
     })
