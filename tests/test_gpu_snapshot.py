@@ -706,20 +706,32 @@ def _pipeline_state(seed):
     return sizes, ts
 
 
-@pytest.mark.parametrize("form", ["fused", "stages"])
+@pytest.mark.parametrize("form", ["fused", "fused16", "stages"])
 @pytest.mark.parametrize("C", [65536, 16384])
-def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monkeypatch):
+def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monkeypatch, tmp_path):
     """Large enough for several allocation groups: the pipelined patch (image
     capacity covers the largest patch) and the serial one (capacity one byte
     short of that bound) both equal the oracle's patch, byte for byte, at 0 %,
     a few and 100 % dirty chunks.  Both pipelined forms: the fused one (one
     cooperative launch whose CTAs hash, lay out and gather group by group,
-    the default) and the launch-per-stage one (SNAP_FUSED_OFF)."""
+    the default), also with a 16-warp hash shape taken from the tuning cache
+    (the general kernel instantiation, 512-thread CTAs), and the
+    launch-per-stage one (SNAP_FUSED_OFF)."""
+    import math
     if form == "stages":
         monkeypatch.setenv("SNAP_FUSED_OFF", "1")
     sizes, ts = _pipeline_state(31)
+    if form == "fused16":
+        cache = tmp_path / "tune.jsonl"
+        cls = int(math.floor(math.log2(sum(sizes))))
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        cache.write_text('{"gpu": "%s", "op": 1, "chunk": %d, "class": %d, "warps": 16, "stages": 2, "piece": 64, '
+                         '"chains": 1, "tma": 0, "ctas": %d, "gbs": 1.0}\n' % (torch.cuda.get_device_name(), C, cls, sms))
+        monkeypatch.setenv("SNAP_TUNE_CACHE", str(cache))
     a = make_set(ts, C)
     b = make_set(ts, C)
+    if form == "fused16":
+        assert a.tuning(snap.INCREMENTAL)["warps"] == 16
     full_a = snap.HostBuffer(a.image_bytes(snap.FULL))
     full_b = snap.HostBuffer(b.image_bytes(snap.FULL))
     bound = a.image_bytes(snap.INCREMENTAL)
@@ -750,7 +762,7 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         assert used_a == exp.size and np.array_equal(pa.view(used_a), exp), name
         assert used_b == exp.size and np.array_equal(pb.view(used_b), exp), name
         assert st_a["dirty_chunks"] == st_b["dirty_chunks"] == nd
-        if form == "fused":  # one fused launch between the two phase stamps
+        if form != "stages":  # one fused launch between the two phase stamps
             assert st_a["kernel_launches"] == 3
         else:  # the launch-per-stage sequence ran
             assert st_a["kernel_launches"] > st_b["kernel_launches"]
