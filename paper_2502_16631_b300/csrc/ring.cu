@@ -41,9 +41,12 @@ struct Ring {
     std::vector<cudaEvent_t> ev0;  // one per slot: the start of that kernel (device timing)
     Pool *pool = nullptr;       // copy workers: checkpoint drains, file reads
     Pool *fill_pool = nullptr;  // fewer workers for restore fills from memory images
-    Job *d_jobs = nullptr;   // one job per slot (device)
-    Job *h_jobs = nullptr;   // pinned staging
-    unsigned long long *d_cursor = nullptr;  // one cursor per slot
+    // one job and one tile cursor per window of the current call, uploaded
+    // and zeroed once at its start (grown as calls need, never shrunk)
+    Job *d_wjobs = nullptr;
+    Job *h_wjobs = nullptr;  // pinned staging
+    unsigned long long *d_wcursor = nullptr;
+    size_t wcap = 0;
 };
 
 void ring_free(snap_set_s *s)
@@ -56,9 +59,9 @@ void ring_free(snap_set_s *s)
     for (auto e : r->ev) if (e) cudaEventDestroy(e);
     for (auto e : r->ev0) if (e) cudaEventDestroy(e);
     cudaFreeHost(r->host);
-    cudaFree(r->d_jobs);
-    cudaFreeHost(r->h_jobs);
-    cudaFree(r->d_cursor);
+    cudaFree(r->d_wjobs);
+    cudaFreeHost(r->h_wjobs);
+    cudaFree(r->d_wcursor);
     delete r;
     s->ring = nullptr;
 }
@@ -82,9 +85,6 @@ int ring_get(snap_set_s *s, Ring **out)
     cudaError_t e = cudaHostAlloc((void **)&r->host, r->bytes, cudaHostAllocMapped | cudaHostAllocPortable);
     if (e == cudaSuccess) r->dev = mapped_device_ptr(r->host);
     if (e == cudaSuccess && !r->dev) e = cudaErrorInvalidValue;
-    if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_jobs, sizeof(Job) * slots);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&r->h_jobs, sizeof(Job) * slots, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_cursor, sizeof(unsigned long long) * slots);
     r->ev.assign(slots, nullptr);
     r->ev0.assign(slots, nullptr);
     for (int i = 0; i < slots && e == cudaSuccess; ++i) e = cudaEventCreate(&r->ev[i]);
@@ -113,21 +113,37 @@ int ring_get(snap_set_s *s, Ring **out)
     return SNAP_OK;
 }
 
-std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes)
+// With `taper`, the first windows grow from kTaperBytes (doubling) and the
+// last ones shrink to it (at most half of what is left): the first window's
+// transfer and the last window's host copy are the two steps of a ring call
+// that nothing overlaps, so they are kept short.
+constexpr uint64_t kTaperBytes = 16ull << 20;
+
+std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes, bool taper)
 {
     std::vector<Window> w;
     Window cur{0, 0, 0, 0};
+    const uint64_t end = s->desc.empty() ? 0 : s->desc.back().state_off + s->desc.back().bytes;
+    uint64_t target = slot_bytes;
     for (size_t k = 0; k < s->desc.size(); ++k) {
         const AllocDesc &a = s->desc[k];
         const uint64_t nk = (a.bytes + s->C - 1) / s->C;
         for (uint64_t i = 0; i < nk; ++i) {
             const uint64_t L = std::min<uint64_t>(s->C, a.bytes - i * s->C);
             const uint64_t b = a.state_off + i * s->C;
-            if (cur.c1 > cur.c0 && (b + L) - cur.b0 > slot_bytes) {
+            if (cur.c1 > cur.c0 && (b + L) - cur.b0 > target) {
                 w.push_back(cur);
                 cur = Window{cur.c1, cur.c1, b, b};
             }
-            if (cur.c1 == cur.c0) cur.b0 = b;
+            if (cur.c1 == cur.c0) {
+                cur.b0 = b;
+                target = slot_bytes;
+                if (taper) {
+                    const uint64_t head = w.size() < 16 ? kTaperBytes << w.size() : slot_bytes;
+                    const uint64_t tail = std::max<uint64_t>(kTaperBytes, (end - b) / 2);
+                    target = std::min(slot_bytes, std::min(head, tail));
+                }
+            }
             cur.c1 = a.chunk0 + i + 1;
             cur.b1 = b + L;
         }
@@ -237,16 +253,52 @@ static Job window_job(const snap_set_s *s, Ring *r, int slot, uint32_t op, const
     return j;
 }
 
-// Launch one window's tile kernel into its slot between the slot's two
-// events (start, end).
-static cudaError_t launch_window(snap_set_s *s, Ring *r, int slot, const Job &j, const TileShape &sh,
+// Room for n window jobs in the ring's per-call table.  A call starts with
+// no earlier work of the set still running (settle), so the old table can go.
+static int window_table(snap_set_s *s, Ring *r, size_t n)
+{
+    if (n <= r->wcap) return SNAP_OK;
+    cudaStreamSynchronize(s->st);
+    cudaFree(r->d_wjobs);
+    cudaFreeHost(r->h_wjobs);
+    cudaFree(r->d_wcursor);
+    r->d_wjobs = r->h_wjobs = nullptr;
+    r->d_wcursor = nullptr;
+    r->wcap = 0;
+    const size_t cap = std::max<size_t>(n, 64);
+    cudaError_t e = cudaMalloc((void **)&r->d_wjobs, sizeof(Job) * cap);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&r->h_wjobs, sizeof(Job) * cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&r->d_wcursor, sizeof(unsigned long long) * cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(r->d_wjobs);
+        cudaFreeHost(r->h_wjobs);
+        cudaFree(r->d_wcursor);
+        r->d_wjobs = r->h_wjobs = nullptr;
+        r->d_wcursor = nullptr;
+        return SNAP_ENOMEM;
+    }
+    r->wcap = cap;
+    return SNAP_OK;
+}
+
+// One copy of the call's window jobs (h_wjobs[0..n)) and one clear of their
+// cursors, ahead of every window's launch on the library stream.
+static cudaError_t upload_windows(snap_set_s *s, Ring *r, size_t n)
+{
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(r->d_wjobs, r->h_wjobs, sizeof(Job) * n, cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_wcursor, 0, sizeof(unsigned long long) * n, s->st);
+    return e;
+}
+
+// Launch window w's tile kernel into its slot between the slot's two events
+// (start, end).
+static cudaError_t launch_window(snap_set_s *s, Ring *r, size_t w, int slot, const TileShape &sh,
                                  const CombineConsts &cc)
 {
-    r->h_jobs[slot] = j;
-    cudaError_t e = cudaMemcpyAsync(r->d_jobs + slot, r->h_jobs + slot, sizeof(Job), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_cursor + slot, 0, sizeof(unsigned long long), s->st);
-    if (e == cudaSuccess) e = cudaEventRecord(r->ev0[slot], s->st);
-    if (e == cudaSuccess) e = launch_tiles(r->d_jobs + slot, 1, r->d_cursor + slot, cc, sh, &s->d_cb->res, s->st);
+    cudaError_t e = cudaEventRecord(r->ev0[slot], s->st);
+    if (e == cudaSuccess) e = launch_tiles(r->d_wjobs + w, 1, r->d_wcursor + w, cc, sh, &s->d_cb->res, s->st);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev[slot], s->st);
     return e;
 }
@@ -306,17 +358,21 @@ static void drain(Progress &pg)
 static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double deadline, int cur, snap_stats &st)
 {
     if (cap < s->full_bytes) return SNAP_EINVAL;
-    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r));
+    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r), true);
     const size_t W = win.size();
     Progress pg;
     pg.left.assign(W, 0);
     pg.launched.assign(W, 0);
+    int rc = window_table(s, r, W);
+    if (rc) return rc;
+    for (size_t w = 0; w < W; ++w)
+        r->h_wjobs[w] = window_job(s, r, (int)(w % r->slots), OP_GATHER, win[w], s->d_hash[cur]);
     std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
     s->h_cb->res.first_bad = ~0ull;
     cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, offsetof(CallBlock, jobs), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = upload_windows(s, r, W);
     const TileShape sh = s->shape[SHAPE_GATHER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
-    int rc = SNAP_OK;
     double kms = 0.0;
     for (size_t w = 0; w < W && e == cudaSuccess && rc == SNAP_OK; ++w) {
         const int slot = (int)(w % r->slots);
@@ -327,7 +383,7 @@ static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double d
             if (rc) break;
             kms += slot_kernel_ms(r, slot);  // its copy-out waited for the kernel
         }
-        e = launch_window(s, r, slot, window_job(s, r, slot, OP_GATHER, win[w], s->d_hash[cur]), sh, cc);
+        e = launch_window(s, r, w, slot, sh, cc);
         if (e != cudaSuccess) break;
         const uint64_t nbytes = win[w].b1 - win[w].b0;
         const uint64_t np = parts_for(nbytes, r->pool->size());
@@ -461,7 +517,24 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
     const TileShape shg = s->shape[SHAPE_GATHER];
     const CombineConsts ccg = make_combine_consts(s->C, shg.piece);
     double kms = 0.0;
-    int rc = SNAP_OK;
+    int rc = window_table(s, r, W);
+    if (rc) return rc;
+    for (size_t w = 0; w < W; ++w) {
+        const uint64_t r0 = w * per, r1 = std::min<uint64_t>(nd, r0 + per);
+        Job j{};
+        j.allocs = s->d_allocs;
+        j.n_allocs = na;
+        j.chunk_bytes = s->C;
+        j.tile_list = s->d_dlist + r0;
+        j.n_tiles = r1 - r0;
+        j.host = r->dev + (uint64_t)(w % r->slots) * r->slot_bytes;
+        j.op = OP_GATHER_DIRTY;
+        j.layout = LAYOUT_PACKED;
+        j.res = &s->d_cb->res;
+        r->h_wjobs[w] = j;
+    }
+    e = upload_windows(s, r, W);
+    if (e != cudaSuccess) return cuda_status(e);
     for (size_t w = 0; w < W && rc == SNAP_OK; ++w) {
         const int slot = (int)(w % r->slots);
         if (w >= (size_t)r->slots) {
@@ -472,17 +545,7 @@ static int ring_incremental(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, d
             kms += slot_kernel_ms(r, slot);
         }
         const uint64_t r0 = w * per, r1 = std::min<uint64_t>(nd, r0 + per);
-        Job j{};
-        j.allocs = s->d_allocs;
-        j.n_allocs = na;
-        j.chunk_bytes = s->C;
-        j.tile_list = s->d_dlist + r0;
-        j.n_tiles = r1 - r0;
-        j.host = r->dev + (uint64_t)slot * r->slot_bytes;
-        j.op = OP_GATHER_DIRTY;
-        j.layout = LAYOUT_PACKED;
-        j.res = &s->d_cb->res;
-        e = launch_window(s, r, slot, j, shg, ccg);
+        e = launch_window(s, r, w, slot, shg, ccg);
         if (e != cudaSuccess) {
             rc = cuda_status(e);
             break;
@@ -584,15 +647,19 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
     int rc = ring_get(s, &r);
     if (rc) return rc;
     const int cur = 1 - s->prev_idx;
-    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r));
+    const std::vector<Window> win = make_windows(s, ring_window_bytes(s, r), true);
     const size_t W = win.size();
     Progress pg;
     pg.left.assign(W, 0);
     pg.launched.assign(W, 0);
+    rc = window_table(s, r, W);
+    if (rc) return rc;
+    for (size_t w = 0; w < W; ++w) r->h_wjobs[w] = window_job(s, r, (int)(w % r->slots), OP_SCATTER, win[w], nullptr);
     std::memset(s->h_cb, 0, offsetof(CallBlock, jobs));
     cudaError_t e = cudaMemcpyAsync(s->d_cb, s->h_cb, offsetof(CallBlock, jobs), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess && s->n_chunks)
         e = cudaMemcpyAsync(s->d_hash[cur], s->h_hash_stage, s->n_chunks * 4, cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = upload_windows(s, r, W);
     if (e != cudaSuccess) return cuda_status(e);
     const TileShape sh = s->shape[SHAPE_SCATTER];
     const CombineConsts cc = make_combine_consts(s->C, sh.piece);
@@ -633,7 +700,7 @@ int ring_restore(snap_set_s *s, ImageIO &io, const ImageHeader &h, double t0, do
         if (pg.err) rc = pg.err;
         if (rc) break;
         if (w >= (size_t)r->slots) kms += slot_kernel_ms(r, slot);  // its fill waited for that kernel
-        e = launch_window(s, r, slot, window_job(s, r, slot, OP_SCATTER, win[w], nullptr), sh, cc);
+        e = launch_window(s, r, w, slot, sh, cc);
         if (e != cudaSuccess) {
             rc = cuda_status(e);
             break;

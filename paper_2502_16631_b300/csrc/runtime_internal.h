@@ -201,7 +201,7 @@ int ring_get(snap_set_s *s, Ring **out);  // allocate the ring on first use
 struct Window {
     uint64_t c0, c1, b0, b1;
 };
-std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes);
+std::vector<Window> make_windows(const snap_set_s *s, uint64_t slot_bytes, bool taper = false);
 void copy_window_part(const snap_set_s *s, const Window &w, uint8_t *slot, uint8_t *image, uint64_t p0, uint64_t p1,
                       bool to_image);
 uint64_t parts_for(uint64_t bytes, int threads);
