@@ -322,12 +322,12 @@ SNAP_API int snap_hash_chunks(const void *dptr, uint64_t bytes, uint64_t chunk_b
  * its scratch is a fixed device array inside libsnap that every GPU using
  * the library keeps until the process exits.  Limits: n_buffers <=
  * SNAP_NOALLOC_MAX_BUFFERS, else SNAP_EINVAL with nothing launched.  The
- * first call on each device looks up that array (cudaGetSymbolAddress):
- * make it before any stream capture.  Calls share the array: two calls
- * whose GPU work overlaps (other streams or threads on the same device)
- * race; this process's host calls are serialised.  Every call copies its
- * descriptor block from host memory onto `stream`, runs there, and
- * synchronises `stream` before it returns. */
+ * first call on each device looks up that array (cudaGetSymbolAddress).
+ * Calls share the array: two calls whose GPU work overlaps (other streams
+ * or threads on the same device) race; this process's host calls are
+ * serialised.  Every call copies its descriptor block from pageable host
+ * memory onto `stream`, runs there, and synchronises `stream` before it
+ * returns, so it must never be made while `stream` is being captured. */
 #define SNAP_NOALLOC_MAX_BUFFERS 1024u
 SNAP_API int snap_hash_chunks_noalloc(const void *const *dptrs, const uint64_t *bytes, uint32_t n_buffers,
                                       uint64_t chunk_bytes, uint32_t *hashes, void *stream);

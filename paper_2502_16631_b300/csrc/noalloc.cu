@@ -22,10 +22,11 @@
 //    calls from one process with a mutex; the GPU side is the caller's to
 //    order.
 //  - the first call on each device looks up the array's device address
-//    (cudaGetSymbolAddress) and opts the kernel into its shared memory; make
-//    that first call before any stream capture;
-//  - every call copies its descriptor block to the device from a static
-//    host block and synchronises the caller's stream before it returns.
+//    (cudaGetSymbolAddress) and opts the kernel into its shared memory;
+//  - every call copies its descriptor block to the device from a static,
+//    pageable host block and synchronises the caller's stream before it
+//    returns, so no call may be made while that stream is being captured
+//    into a CUDA graph.
 #include "snap.h"
 #include "runtime_internal.h"
 
