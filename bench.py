@@ -74,6 +74,8 @@ def parse():
                    "background part)")
     p.add_argument("--async-ctas", default="0,4,37", help="async: background grids to measure (0: the "
                    "library default, which gives the reported value)")
+    p.add_argument("--incr-chunks", default="16,32,64,128,256,512,1024",
+                   help="incr20g: chunk sizes of the sweep (KiB, comma-separated)")
     p.add_argument("--arrivals", type=int, default=1200, help="serving: requests")
     p.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     p.add_argument("--serve-pool-gib", type=int, default=24, help="serving: pinned staging pool (GiB, within "
@@ -789,7 +791,8 @@ def run_incr20g(args, rank, world, local, pg):
     grid = arena.view(-1, UNIT)
     fracs = [0.01, 0.10, 0.50]
     units = {f: torch.from_numpy(dirty_units(sizes, starts, f, args.seed + int(f * 1000))).cuda() for f in fracs}
-    chunks = [16 * KiB, 32 * KiB, 64 * KiB, 128 * KiB, 256 * KiB, 512 * KiB, 1024 * KiB]
+    # 64 KiB is always swept: the plain form and the copy-form comparison use it
+    chunks = sorted({int(x) * KiB for x in args.incr_chunks.split(",")} | {64 * KiB})
     sets = {}
     cap_full = cap_patch = 0
     for C in chunks:
@@ -813,31 +816,48 @@ def run_incr20g(args, rank, world, local, pg):
     table, tune, kern = {}, {}, 0
     clocks = ClockSampler(local)
     clocks.start()
+
+    def measure(s, f):
+        nonlocal kern
+        times, dirty, hashms, copies = [], [], [], []
+        for i in range(3 + 10):
+            grid[units[f]] ^= 0x5A  # the training step: every byte of each chosen unit changes
+            torch.cuda.synchronize()
+            a, b = _ev(), _ev()
+            a.record()
+            used = s.checkpoint(patch, snap.INCREMENTAL)
+            b.record()
+            torch.cuda.synchronize()
+            st = s.stats()
+            if i >= 3:
+                times.append(a.elapsed_time(b))
+                dirty.append(st["dirty_chunks"])
+                hashms.append(st["hash_ms"])
+                copies.append(st["dma_copies"])
+                kern += st["kernel_launches"]
+        assert s.verify(patch, used) == 0
+        ms = statistics.median(times)
+        return {"ms": ms, "effective_gbs": B / (ms * 1e-3) / 1e9, "dirty_chunks": int(statistics.median(dirty)),
+                "hash_ms": statistics.median(hashms), "vs_plain_full": (B / (ms * 1e-3) / 1e9) / plain_gbs,
+                "dma_copies": int(statistics.median(copies))}
+
     for C in chunks:
         s = sets[C]
         tune[C] = s.autotune(snap.INCREMENTAL)
         s.checkpoint(full, snap.FULL)
-        table[C] = {}
-        for f in fracs:
-            times, dirty, hashms = [], [], []
-            for i in range(3 + 10):
-                grid[units[f]] ^= 0x5A  # the training step: every byte of each chosen unit changes
-                torch.cuda.synchronize()
-                a, b = _ev(), _ev()
-                a.record()
-                used = s.checkpoint(patch, snap.INCREMENTAL)
-                b.record()
-                torch.cuda.synchronize()
-                st = s.stats()
-                if i >= 3:
-                    times.append(a.elapsed_time(b))
-                    dirty.append(st["dirty_chunks"])
-                    hashms.append(st["hash_ms"])
-                    kern += st["kernel_launches"]
-            assert s.verify(patch, used) == 0
-            ms = statistics.median(times)
-            table[C][f] = {"ms": ms, "effective_gbs": B / (ms * 1e-3) / 1e9, "dirty_chunks": int(statistics.median(dirty)),
-                           "hash_ms": statistics.median(hashms), "vs_plain_full": (B / (ms * 1e-3) / 1e9) / plain_gbs}
+        table[C] = {f: measure(s, f) for f in fracs}
+    # both ways of moving the dirty chunks, on the same state at 64 KiB
+    # chunks: gather CTAs of the fused launch (SM loads and stores) and the
+    # copy engines (one copy per dirty run, every SM but one hashing)
+    forms = {}
+    for name, mode in (("sm", snap.INCR_COPY_SM), ("dma", snap.INCR_COPY_DMA)):
+        s = snap.Set(chunk_bytes=64 * KiB, incr_copy=mode)
+        for v in views:
+            s.register(v)
+        s.autotune(snap.INCREMENTAL)
+        s.checkpoint(full, snap.FULL)
+        forms[name] = {f: measure(s, f) for f in fracs}
+        s.close()
     clk = clocks.stop()
     best = {f: max(chunks, key=lambda C: table[C][f]["effective_gbs"]) for f in fracs}
     v10 = table[best[0.10]][0.10]
@@ -867,6 +887,9 @@ def run_incr20g(args, rank, world, local, pg):
                               "note": "10 % case; roofline = max(state bytes / measured HBM, dirty bytes / "
                                       "measured D2H copy rate)"},
                  "roofline_by_frac": {str(int(f * 100)) + "%": roof(f) for f in fracs},
+                 "copy_forms_64KiB": {name: {str(int(f * 100)) + "%": dict(
+                     t, roofline_frac=max(B / (pk * 1e9), t["dirty_chunks"] * 64 * KiB / (link * 1e9)) * 1e3 / t["ms"])
+                     for f, t in tab.items()} for name, tab in forms.items()},
                  "roofline_hash": {"bound": "hbm", "kernel": "snap_tiles (OP_HASH)", "achieved": hash_gbs,
                                    "peak": pk, "unit": "GB/s", "frac": hash_gbs / pk,
                                    "note": "the autotuner's timing of the hash pass alone, best chunk size"},

@@ -93,7 +93,18 @@ typedef struct {
     uint32_t hash_tma;     /* 1: stage the hash pass with 2D TMA tensor copies
                               (else per-lane cp.async; snap_autotune may
                               change it) */
+    uint32_t incr_copy;    /* how a pipelined incremental checkpoint into a
+                              pinned image moves its dirty chunks while the
+                              hash pass runs: SNAP_INCR_COPY_DMA (the launch
+                              lists each group's runs of consecutive dirty
+                              chunks in mapped host memory and the calling
+                              thread hands each run to the copy engines, so
+                              every SM but one hashes) or SNAP_INCR_COPY_SM
+                              (gather CTAs of the same launch, SM loads and
+                              stores); 0 = $SNAP_INCR_COPY ("sm" / "dma") when
+                              set, else DMA */
 } snap_opts;
+enum { SNAP_INCR_COPY_DEFAULT = 0, SNAP_INCR_COPY_SM = 1, SNAP_INCR_COPY_DMA = 2 };
 
 /* Per-call statistics (times in milliseconds; quiesce_ms and total_ms are
  * host wall time, the others come from CUDA events on the library stream). */
@@ -121,6 +132,8 @@ typedef struct {
                                 where the CRC lookups expect it.  Unlike the
                                 other fields it is not the last successful
                                 call's. */
+    uint64_t dma_copies;     /* copy-engine copies of dirty runs the call
+                                issued (incremental, SNAP_INCR_COPY_DMA) */
 } snap_stats;
 
 /* ------------------------------------------------------------------ sets */
@@ -187,7 +200,12 @@ SNAP_API int snap_host_unregister(void *p);
  *    dirty chunks and only their bytes.  Needs a committed base (ENOBASE).
  * Steps: quiesce the caller's stream with the deadline (the "lock",
  * Sec. 3.1.1), run the graph-captured persistent kernels, wait with the
- * deadline, then commit the new hash table and generation.  *used receives
+ * deadline, then commit the new hash table and generation.  An incremental
+ * checkpoint of a state large enough to pipeline, into a pinned image whose
+ * capacity covers the largest patch, moves its dirty chunks as
+ * opts.incr_copy says: by default the calling thread hands each run of
+ * dirty chunks the launch lists to the copy engines while the launch is
+ * still hashing (the patch bytes are the same either way).  *used receives
  * the image size.  Errors: EINVAL (cap too small: nothing committed),
  * ENOBASE, ETIMEDOUT, EBUSY, ENOMEM, ECUDA. */
 SNAP_API int snap_checkpoint(snap_set s, void *host_image, uint64_t cap, int mode, uint64_t *used);

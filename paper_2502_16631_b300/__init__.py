@@ -28,6 +28,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ENOBASE, EFORMAT, EMISMATCH, EBUSY, EBUDGE
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11
 FILE_SYNC = 1
 FULL, INCREMENTAL = 0, 1
+INCR_COPY_DEFAULT, INCR_COPY_SM, INCR_COPY_DMA = 0, 1, 2
 REQ_FULL, REQ_INCREMENTAL, REQ_RESTORE = 0, 1, 2
 
 # Every entry point declared in include/snap.h.
@@ -54,7 +55,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint64), ("timeout_ms", ctypes.c_uint32),
                 ("device", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("ctas_per_sm", ctypes.c_uint32), ("stages", ctypes.c_uint32),
-                ("ring_bytes", ctypes.c_uint64), ("async_ctas", ctypes.c_uint32), ("hash_tma", ctypes.c_uint32)]
+                ("ring_bytes", ctypes.c_uint64), ("async_ctas", ctypes.c_uint32), ("hash_tma", ctypes.c_uint32),
+                ("incr_copy", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -64,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("quiesce_ms", ctypes.c_double), ("hash_ms", ctypes.c_double),
                 ("diff_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("kernel_launches", ctypes.c_uint64),
-                ("frozen_ms", ctypes.c_double), ("device_errors", ctypes.c_uint64)]
+                ("frozen_ms", ctypes.c_double), ("device_errors", ctypes.c_uint64),
+                ("dma_copies", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -214,9 +217,9 @@ class Set:
 
     def __init__(self, chunk_bytes: int = 0, timeout_ms: int = 0, device: int = -1, stream=None,
                  ctas_per_sm: int = 0, stages: int = 0, ring_bytes: int = 0, async_ctas: int = 0,
-                 hash_tma: bool = False):
+                 hash_tma: bool = False, incr_copy: int = 0):
         o = Opts(chunk_bytes, timeout_ms, device, _stream_handle(stream), ctas_per_sm, stages, ring_bytes,
-                 async_ctas, 1 if hash_tma else 0)
+                 async_ctas, 1 if hash_tma else 0, incr_copy)
         h = ctypes.c_void_p()
         _check(_lib().snap_set_create(ctypes.byref(h), ctypes.byref(o)), "snap_set_create")
         self.h = h.value

@@ -694,6 +694,64 @@ __device__ __forceinline__ int fused_group(const FusedIncr &f, uint64_t chunk)
     return lo;
 }
 
+// Copy-engine form, metadata CTA: list group g's dirty runs (dirty entries
+// [beg, end) of the ascending list, laid out already) after the *nruns runs
+// of earlier groups, then publish the group to the host: entries first,
+// then its begin and count, then, after a system-scope fence, ready = 1.
+// A run is a maximal range of consecutive dirty chunks of one allocation;
+// its patch slots are contiguous (a full chunk fills its C-byte slot), so
+// one copy moves it.  With `use` false (the patch would pass the image
+// capacity) the group is published with no runs.
+__device__ void fused_list_runs(const Job &jb, FusedIncr &f, int g, unsigned long long beg,
+                                unsigned long long end, bool use, unsigned long long *nruns,
+                                unsigned long long *ws)
+{
+    const uint64_t C = jb.chunk_bytes;
+    const unsigned long long first = *nruns;
+    // starts and ends listed so far: a run may start in one pass of the loop
+    // and end in a later one, so each side keeps its own count
+    unsigned long long n = first, ne = first;
+    for (unsigned long long base = beg; use && base < end; base += blockDim.x) {
+        const unsigned long long r = base + threadIdx.x;
+        bool st = false, en = false;
+        uint64_t k = 0, i = 0, slot = 0, L = 0;
+        if (r < end) {
+            const uint64_t c = f.dlist[r];
+            k = find_alloc(jb.allocs, jb.n_allocs, c);
+            const AllocDesc a = jb.allocs[k];
+            const uint64_t nk = (a.bytes + C - 1) / C;
+            i = c - a.chunk0;
+            st = r == beg || f.dlist[r - 1] + 1 != c || i == 0;
+            en = r + 1 == end || f.dlist[r + 1] != c + 1 || i + 1 == nk;
+            slot = f.patch_data[k] + (r - f.dstart[k]) * C;
+            L = (a.bytes - i * C) < C ? (a.bytes - i * C) : C;
+        }
+        unsigned long long ts, te;
+        const unsigned long long xs = cta_exscan(st ? 1ull : 0ull, &ts, ws);
+        const unsigned long long xe = cta_exscan(en ? 1ull : 0ull, &te, ws);
+        // the i-th start and the i-th end of the list belong to the same run
+        if (st && n + xs < f.runs_cap) {
+            DirtyRun *d = f.runs + n + xs;
+            d->alloc = k;
+            d->chunk = i;
+            d->dst0 = slot;
+        }
+        if (en && ne + xe < f.runs_cap) f.runs[ne + xe].dst1 = slot + L;
+        n += ts;
+        ne += te;
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile RunGroup *p = f.pub + g;
+        p->begin = first;
+        p->count = n - first;
+        __threadfence_system();
+        p->ready = 1ull;
+    }
+    *nruns = n;
+}
+
 // The metadata role (one CTA): per group, in order, once its chunks are
 // hashed: the dirty list (ascending, continuing the running count), the
 // patch layout of its allocations (continuing the running offset; the
@@ -705,6 +763,7 @@ __device__ void fused_meta(const Job &jb, FusedIncr &f, unsigned long long *ws, 
     const uint32_t *cur = jb.hash_out;
     unsigned long long run = 0;    // dirty entries listed so far
     unsigned long long off = 64;   // patch offset of the next record
+    unsigned long long nruns = 0;  // copy-engine form: dirty runs listed so far
     if (threadIdx.x == 0) kres->ts[TS_DIFF_END] = global_ns();  // the whole pipeline is copy time
     for (int g = 0; g < f.n_groups; ++g) {
         const uint64_t c0 = f.gch[g], c1 = f.gch[g + 1];
@@ -773,9 +832,20 @@ __device__ void fused_meta(const Job &jb, FusedIncr &f, unsigned long long *ws, 
                 uint32_t *z = reinterpret_cast<uint32_t *>(f.host + zlo);
                 const uint64_t nz = (data - zlo) / 4;
                 for (uint64_t q = lane; q < nz; q += 32) z[q] = 0u;
+                // copy-engine form: the copies carry data bytes only, so the
+                // padding after a dirty partial last chunk is zeroed here
+                if (f.dma && nd) {
+                    const uint64_t Ll = a.bytes - (nk - 1) * C;
+                    if ((Ll & 4095u) && f.dlist[ds + nd - 1] == a.chunk0 + nk - 1)
+                        warp_zero(f.host + data + (nd - 1) * C + Ll, up_page(Ll) - Ll, lane);
+                }
             }
         }
         __syncthreads();
+        if (f.dma) {
+            fused_list_runs(jb, f, g, beg, run, off <= f.cap, &nruns, ws);
+            continue;
+        }
         if (threadIdx.x == 0) {
             f.gbeg[g] = beg;
             f.gcnt[g] = off <= f.cap ? run - beg : 0ull;  // over capacity: nothing is gathered

@@ -27,6 +27,10 @@ constexpr int kMaxPipe = 2 * kMaxGroups;
 // CTAs that gather dirty chunks while the other SMs hash the next group: the
 // device-to-host link saturates with 8 gather CTAs on B300.
 constexpr int kPipeGatherCtas = 8;
+// Copy streams of the fused incremental's copy-engine form: at most this
+// many, one by default ($SNAP_DMA_STREAMS): runs dealt over four streams made
+// the 1 % incremental of a 20 GiB state 19 % slower on B300, not faster.
+constexpr int kDmaStreams = 4;
 
 // Everything one launch sequence needs that changes from call to call; the
 // host fills a pinned copy and the captured graph's first node copies it in.
@@ -104,6 +108,18 @@ struct snap_set_s {
     uint64_t gal[snapk::kMaxPipe + 1] = {}, gch[snapk::kMaxPipe + 1] = {};
     cudaStream_t st_pipe = nullptr, st_meta = nullptr;
     cudaEvent_t ev_pipe[2 * snapk::kMaxPipe + 1] = {};
+
+    // fused incremental, copy-engine form: the group records and run table
+    // (one pinned, mapped block), the copy stream, and the current call's
+    // choice and copy count
+    snapk::RunGroup *h_rungrp = nullptr;  // kFusedMaxGroups records, then runs_cap runs
+    snapk::DirtyRun *h_runs = nullptr;
+    uint64_t runs_cap = 0;
+    cudaStream_t st_dma[snapk::kDmaStreams] = {};
+    cudaEvent_t ev_dma[snapk::kDmaStreams] = {};
+    cudaEvent_t ev_graph_end = nullptr;
+    bool dma_call = false;
+    uint64_t dma_copies = 0;
 
     std::vector<snapk::GraphEntry> graphs;
     snapk::TileShape shape[snapk::SHAPE_COUNT];

@@ -97,12 +97,33 @@ struct Job {
 // its group; CTA n_hash_ctas waits for each group in turn and diffs it
 // (ascending dirty list), lays out its allocations' patch records and
 // writes their metadata into the patch; the remaining CTAs wait for each
-// group's metadata and copy its dirty chunks into their patch slots.  A
+// group's metadata and copy its dirty chunks into their patch slots (or,
+// with `dma`, there are none: the metadata CTA lists the group's dirty runs
+// for the copy engines instead, see DirtyRun).  A
 // group is a run of whole allocations, chunks [gch[g], gch[g+1]) and
 // allocations [gal[g], gal[g+1]).  Every wait is bounded (ERR_WAIT_TIMEOUT);
 // the cooperative launch keeps every CTA resident, so no role waits on a CTA
 // that is not running.
 constexpr int kFusedMaxGroups = 64;
+
+// Copy-engine form of the fused incremental's dirty copy: the metadata CTA
+// lists each group's dirty runs (maximal ranges of consecutive dirty chunks
+// of one allocation; their patch slots are contiguous) in pinned, mapped
+// host memory and publishes the group; a host thread hands every run to the
+// copy engines (one asynchronous device-to-host copy each) while the SMs
+// hash the later groups.  Host and device agree on these two layouts.
+struct DirtyRun {
+    uint64_t alloc;  // allocation index
+    uint64_t chunk;  // first chunk of the run, within the allocation
+    uint64_t dst0;   // patch offset of the run's first byte
+    uint64_t dst1;   // patch offset one past its last data byte
+};
+struct RunGroup {
+    unsigned long long begin, count;  // the group's runs: entries [begin, begin + count)
+    unsigned long long ready;         // written last, 1 once begin and count and the entries are
+    unsigned long long pad;
+};
+
 struct FusedIncr {
     const uint32_t *prev;      // committed hashes
     uint32_t *dlist;           // ascending dirty chunk list
@@ -110,6 +131,11 @@ struct FusedIncr {
     uint8_t *host;             // device-visible address of the patch image
     uint64_t cap;              // its capacity
     int n_groups, n_hash_ctas;
+    int dma;                   // 1: no gather CTAs; runs are listed for the copy engines
+    int pad_;
+    DirtyRun *runs;            // dma: device-visible address of the run table (mapped host)
+    RunGroup *pub;             // dma: device-visible address of the per-group records (mapped host)
+    uint64_t runs_cap;         // dma: entries of the run table
     uint64_t gch[kFusedMaxGroups + 1];
     uint64_t gal[kFusedMaxGroups + 1];
     // counters and results, zero at the start of every call

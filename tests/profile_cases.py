@@ -15,7 +15,10 @@ under `ncu`; not collected by pytest).
     python tests/profile_cases.py fused [reps]    # 8 x 256 MiB, one full checkpoint, then fused
                                                   # incremental checkpoints with 10 % of the
                                                   # chunks changed before each (one cooperative
-                                                  # launch each)
+                                                  # launch each; its dirty runs go to the copy
+                                                  # engines, the default)
+    python tests/profile_cases.py fusedsm [reps]  # the same with the dirty chunks copied by
+                                                  # gather CTAs of the launch (SNAP_INCR_COPY_SM)
 """
 import os
 import sys
@@ -43,11 +46,11 @@ def main():
         img = np.empty(s.image_bytes(snap.FULL), dtype=np.uint8)
         for _ in range(reps + 1):
             s.checkpoint(img, snap.FULL)
-    elif op == "fused":
+    elif op in ("fused", "fusedsm"):
         ts = [torch.empty(256 * MiB, dtype=torch.uint8, device="cuda") for _ in range(8)]
         for t in ts:
             t.random_(0, 256)
-        s = snap.Set(chunk_bytes=65536)
+        s = snap.Set(chunk_bytes=65536, incr_copy=snap.INCR_COPY_SM if op == "fusedsm" else snap.INCR_COPY_DMA)
         for t in ts:
             s.register(t)
         full = snap.HostBuffer(s.image_bytes(snap.FULL))

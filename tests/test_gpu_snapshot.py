@@ -706,7 +706,7 @@ def _pipeline_state(seed):
     return sizes, ts
 
 
-@pytest.mark.parametrize("form", ["fused", "fused16", "stages"])
+@pytest.mark.parametrize("form", ["fused", "fused16", "dma", "stages"])
 @pytest.mark.parametrize("C", [65536, 16384])
 def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monkeypatch, tmp_path):
     """Large enough for several allocation groups: the pipelined patch (image
@@ -715,8 +715,10 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
     a few and 100 % dirty chunks.  Both pipelined forms: the fused one (one
     cooperative launch whose CTAs hash, lay out and gather group by group,
     the default), also with a 16-warp hash shape taken from the tuning cache
-    (the general kernel instantiation, 512-thread CTAs), and the
-    launch-per-stage one (SNAP_FUSED_OFF)."""
+    (the general kernel instantiation, 512-thread CTAs) and with its dirty
+    runs handed to the copy engines (SNAP_INCR_COPY_DMA: one copy per run of
+    consecutive dirty chunks of an allocation), and the launch-per-stage one
+    (SNAP_FUSED_OFF)."""
     import math
     if form == "stages":
         monkeypatch.setenv("SNAP_FUSED_OFF", "1")
@@ -728,7 +730,7 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         cache.write_text('{"gpu": "%s", "op": 1, "chunk": %d, "class": %d, "warps": 16, "stages": 2, "piece": 64, '
                          '"chains": 1, "tma": 0, "ctas": %d, "gbs": 1.0}\n' % (torch.cuda.get_device_name(), C, cls, sms))
         monkeypatch.setenv("SNAP_TUNE_CACHE", str(cache))
-    a = make_set(ts, C)
+    a = make_set(ts, C, incr_copy=snap.INCR_COPY_DMA if form == "dma" else snap.INCR_COPY_SM)
     b = make_set(ts, C)
     if form == "fused16":
         assert a.tuning(snap.INCREMENTAL)["warps"] == 16
@@ -762,8 +764,13 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         assert used_a == exp.size and np.array_equal(pa.view(used_a), exp), name
         assert used_b == exp.size and np.array_equal(pb.view(used_b), exp), name
         assert st_a["dirty_chunks"] == st_b["dirty_chunks"] == nd
-        if form != "stages":  # one fused launch between the two phase stamps
-            assert st_a["kernel_launches"] == 3
+        if form == "dma":  # the fused launch, then a stamp after the copies
+            assert st_a["kernel_launches"] == 4
+            assert (st_a["dma_copies"] > 0) == (nd > 0) and st_a["dma_copies"] <= nd
+            if name == "all":  # one run per allocation with chunks
+                assert st_a["dma_copies"] == sum(1 for n in nch if n)
+        elif form != "stages":  # one fused launch between the two phase stamps
+            assert st_a["kernel_launches"] == 3 and st_a["dma_copies"] == 0
         else:  # the launch-per-stage sequence ran
             assert st_a["kernel_launches"] > st_b["kernel_launches"]
         prev = [oracle.chunk_hashes(h, C) for h in cur]
@@ -772,18 +779,20 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
     b.close()
 
 
-def test_fused_incremental_gives_up_and_the_set_recovers(monkeypatch):
+@pytest.mark.parametrize("copy", ["sm", "dma"])
+def test_fused_incremental_gives_up_and_the_set_recovers(copy, monkeypatch):
     """The fused incremental's device-side waits reach their error path
     without a fault: with the test hook SNAP_TEST_STALL_TILE one hash warp's
     bounded wait runs out; the metadata CTA waiting for that warp's group and
     the gather CTAs waiting for its metadata see the recorded error (or run
-    out themselves) and leave; the call returns SNAP_ECUDA inside the call
-    deadline with nothing committed, and the next incremental (fused again)
-    equals the oracle's patch."""
+    out themselves) and leave (in the copy-engine form the host stops taking
+    groups when the launch ends without publishing the next one); the call
+    returns SNAP_ECUDA inside the call deadline with nothing committed, and
+    the next incremental (fused again) equals the oracle's patch."""
     import time
     C = 65536
     sizes, ts = _pipeline_state(41)
-    s = make_set(ts, C)
+    s = make_set(ts, C, incr_copy=snap.INCR_COPY_DMA if copy == "dma" else snap.INCR_COPY_SM)
     full = snap.HostBuffer(s.image_bytes(snap.FULL))
     patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
     s.checkpoint(full, snap.FULL)
@@ -803,22 +812,27 @@ def test_fused_incremental_gives_up_and_the_set_recovers(monkeypatch):
     assert g2 == gen and np.array_equal(h2, base)
     monkeypatch.delenv("SNAP_TEST_STALL_TILE")
     used = s.checkpoint(patch, snap.INCREMENTAL)
-    assert s.stats()["kernel_launches"] == 3 and s.stats()["device_errors"] == 0  # the fused form, clean
+    launches = 4 if copy == "dma" else 3
+    assert s.stats()["kernel_launches"] == launches and s.stats()["device_errors"] == 0  # the fused form, clean
     rc, exp, nd = oracle.write_patch(cur, C, prev, 1, 0)
     assert rc == 0 and used == exp.size and np.array_equal(patch.view(used), exp)
     s.close()
 
 
-def test_gpt2_state_pipelined_incremental_parity():
+@pytest.mark.parametrize("copy", ["sm", "dma"])
+def test_gpt2_state_pipelined_incremental_parity(copy):
     """GPT-2-small training state (2.26 GB, eight allocation groups): a 10 %
     clustered mutation; the pipelined patch equals the oracle's, and the
-    previous full image plus the patch equals the full image of the state."""
+    previous full image plus the patch equals the full image of the state.
+    Both ways of moving the dirty chunks: gather CTAs, and copy engines (one
+    copy per run of consecutive dirty chunks, many of them single small
+    tensors)."""
     spec = workloads.gpt2_state_spec()
     sizes = workloads.spec_bytes(spec)
     ts = [torch.empty(n, dtype=torch.uint8, device="cuda") for n in sizes]
     workloads.torch_fill_spec(ts, spec, seed=3)
     C = 65536
-    s = make_set(ts, C)
+    s = make_set(ts, C, incr_copy=snap.INCR_COPY_DMA if copy == "dma" else snap.INCR_COPY_SM)
     full = snap.HostBuffer(s.image_bytes(snap.FULL))
     patch = snap.HostBuffer(s.image_bytes(snap.INCREMENTAL))
     used0 = s.checkpoint(full, snap.FULL)
@@ -831,6 +845,7 @@ def test_gpt2_state_pipelined_incremental_parity():
     mutate(ts, C, chunks, seed=5)
     cur = readback(ts)
     used = s.checkpoint(patch, snap.INCREMENTAL)
+    assert (s.stats()["dma_copies"] > 0) == (copy == "dma")
     rc, exp, nd = oracle.write_patch(cur, C, [oracle.chunk_hashes(h, C) for h in base], 1, 0)
     assert rc == 0 and nd == len(set(chunks))
     assert used == exp.size and np.array_equal(patch.view(used), exp)
