@@ -89,3 +89,8 @@ def test_host_only_calls_work_without_a_gpu():
     assert L.snap_link_ceiling(-1, 3, 1 << 20, 1, ctypes.byref(v)) == snap.EINVAL
     t = snap.Tuning()
     assert L.snap_get_tuning(None, 0, ctypes.byref(t)) == snap.EINVAL
+    # set options are checked before the device is touched
+    h = ctypes.c_void_p()
+    for bad in (snap.Opts(chunk_bytes=1000), snap.Opts(chunk_bytes=32 << 20),
+                snap.Opts(incr_copy=snap.INCR_COPY_DMA + 1)):
+        assert L.snap_set_create(ctypes.byref(h), ctypes.byref(bad)) == snap.EINVAL and not h.value
