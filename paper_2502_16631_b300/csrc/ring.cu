@@ -25,6 +25,7 @@
 #include <deque>
 #include <functional>
 #include <mutex>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -346,6 +347,16 @@ static void mark_in_flight(snap_set_s *s)
     else cudaGetLastError();
 }
 
+// Fault injection (SNAP_FAULT=ring_stall, tests only): a checkpoint's
+// copy-out task stalls until just past the call's deadline, as a consumer
+// that stops draining the ring would, so the launcher's wait for a free
+// slot runs out (SNAP_ETIMEDOUT); the task then finishes, so nothing
+// outlives the call.
+static void stall_past(double deadline)
+{
+    while (now_ms() < deadline + 20.0) std::this_thread::sleep_for(std::chrono::milliseconds(1));
+}
+
 // Wait for every queued worker task (bounded); used on every exit path so
 // that no task outlives the caller's buffers.
 static void drain(Progress &pg)
@@ -395,6 +406,7 @@ static int ring_full(snap_set_s *s, Ring *r, ImageIO &io, uint64_t cap, double d
         for (uint64_t p = 0; p < np; ++p) {
             const uint64_t p0 = nbytes * p / np, p1 = nbytes * (p + 1) / np;
             r->pool->push([&, w, slot, p0, p1] {
+                if (fault_injected("ring_stall")) stall_past(deadline);
                 if (!pg.err) {
                     const int q = wait_event(r->ev[slot], deadline);  // ETIMEDOUT or ECUDA
                     if (q) pg.err = q;

@@ -627,6 +627,35 @@ def test_quiesce_timeout_then_recovers():
     assert np.array_equal(img.view(used), oracle.write_full(hs, 65536, 0)[1])
 
 
+def test_ring_consumer_stall_times_out_then_recovers(monkeypatch):
+    """A ring consumer that stops draining, injected on the host
+    (SNAP_FAULT=ring_stall: every copy-out task of a checkpoint waits until
+    just past the call's deadline): the launcher's wait for a free slot runs
+    out, the call returns SNAP_ETIMEDOUT soon after the deadline with nothing
+    committed, and the next checkpoint, with the consumer draining again,
+    equals the oracle's image (Sec. 3.1.1: a timeout rolls back)."""
+    import time
+    C = 65536
+    sizes = [3 * 2**20 + 4096, 5 * 2**20, 12345]
+    ts, hs = device_state(sizes, seed=61)
+    s = make_set(ts, C, ring_bytes=2 << 20, timeout_ms=300)  # 8 slots of 256 KiB: 33 windows
+    s.prepare(layout=True, ring=True)
+    full = np.full(s.image_bytes(snap.FULL), 0xA5, dtype=np.uint8)  # pageable: through the ring
+    monkeypatch.setenv("SNAP_FAULT", "ring_stall")
+    t0 = time.perf_counter()
+    rc, _ = s.checkpoint_status(full, snap.FULL)
+    dt = time.perf_counter() - t0
+    assert rc == snap.ETIMEDOUT and dt < 3.0
+    nch = sum((n + C - 1) // C for n in sizes)
+    with pytest.raises(snap.SnapError):
+        s.committed_hashes(nch)  # nothing was committed
+    monkeypatch.delenv("SNAP_FAULT")
+    used = s.checkpoint(full, snap.FULL)
+    assert np.array_equal(full[:used], oracle.write_full(hs, C, 0)[1])
+    assert s.committed_hashes(nch)[1] == 0
+    s.close()
+
+
 def test_injected_allocation_failure_leaves_set_usable(monkeypatch):
     ts, hs = device_state([70000], seed=19)
     s = make_set(ts, 4096)
@@ -712,7 +741,8 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
     """Large enough for several allocation groups: the pipelined patch (image
     capacity covers the largest patch) and the serial one (capacity one byte
     short of that bound) both equal the oracle's patch, byte for byte, at 0 %,
-    a few and 100 % dirty chunks.  Both pipelined forms: the fused one (one
+    a few, every other (alternating: no two dirty chunks adjacent) and 100 %
+    dirty chunks.  Both pipelined forms: the fused one (one
     cooperative launch whose CTAs hash, lay out and gather group by group,
     the default), also with a 16-warp hash shape taken from the tuning cache
     (the general kernel instantiation, 512-thread CTAs) and with its dirty
@@ -749,6 +779,7 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         if n:
             dirty |= {(k, 0), (k, n - 1), (k, int(rng.integers(0, n)))}
     plans = [("none", set()), ("some", dirty),
+             ("alternate", {(k, i) for k, n in enumerate(nch) for i in range(k % 2, n, 2)}),
              ("all", {(k, i) for k, n in enumerate(nch) for i in range(n)})]
     prev = [oracle.chunk_hashes(h, C) for h in base]
     gen = 1
@@ -769,6 +800,8 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
             assert (st_a["dma_copies"] > 0) == (nd > 0) and st_a["dma_copies"] <= nd
             if name == "all":  # one run per allocation with chunks
                 assert st_a["dma_copies"] == sum(1 for n in nch if n)
+            if name == "alternate":  # no two dirty chunks adjacent: a run per chunk
+                assert st_a["dma_copies"] == nd
         elif form != "stages":  # one fused launch between the two phase stamps
             assert st_a["kernel_launches"] == 3 and st_a["dma_copies"] == 0
         else:  # the launch-per-stage sequence ran
