@@ -1229,7 +1229,8 @@ static int run_checkpoint(snap_set_s *s, GraphEntry *ge, uint8_t *image, uint64_
     if (rc) return rc;
     bool bad = false;
     int rc_dma = SNAP_OK;
-    if (s->dma_call) rc_dma = dma_dirty_runs(s, image, cap, deadline, &bad);
+    // the copies stay inside the pinned range the direct path was chosen for
+    if (s->dma_call) rc_dma = dma_dirty_runs(s, image, image_extent(s, SNAP_INCREMENTAL, cap), deadline, &bad);
     rc = finish(s, deadline);
     if (bad) {
         s->device_err |= ERR_BAD_TILE;
