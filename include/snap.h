@@ -102,7 +102,9 @@ typedef struct {
                               every SM but one hashes) or SNAP_INCR_COPY_SM
                               (gather CTAs of the same launch, SM loads and
                               stores); 0 = $SNAP_INCR_COPY ("sm" / "dma") when
-                              set, else DMA */
+                              set, else DMA.  The DMA form allocates, on its
+                              first use, a pinned and mapped run table of 32
+                              bytes per chunk of the set and one copy stream */
 } snap_opts;
 enum { SNAP_INCR_COPY_DEFAULT = 0, SNAP_INCR_COPY_SM = 1, SNAP_INCR_COPY_DMA = 2 };
 
