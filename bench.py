@@ -881,7 +881,8 @@ def run_incr20g(args, rank, world, local, pg):
                  "autotuned_shape": {str(C // KiB) + "KiB": tune[C] for C in chunks},
                  "speedup_vs_plain_full": {str(int(f * 100)) + "%": table[best[f]][f]["vs_plain_full"] for f in fracs},
                  "plain_full_gbs": plain_gbs,
-                 "roofline": {"bound": "host_link", "kernel": "pipelined incremental (hash + diff + dirty gather)",
+                 "roofline": {"bound": "host_link", "kernel": "fused incremental (hash, diff and metadata in one launch; "
+                                                        "dirty runs by the copy engines by default)",
                               "achieved": v10["effective_gbs"], "peak": B / (roof(0.10)["roofline_ms"] * 1e-3) / 1e9,
                               "unit": "GB/s", "frac": roof(0.10)["frac"],
                               "note": "10 % case; roofline = max(state bytes / measured HBM, dirty bytes / "
