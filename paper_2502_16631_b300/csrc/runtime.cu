@@ -1138,16 +1138,8 @@ int snap_image_bytes(snap_set s, int mode, uint64_t *out)
     return SNAP_OK;
 }
 
-// Copy-engine form, host side: while the fused launch runs, take its groups
-// in order as the metadata CTA publishes them and hand each dirty run to
-// the copy engines (one asynchronous copy each, into the caller's pinned
-// image, the runs dealt round-robin over dma_streams() copy streams).
-// Each entry is checked against the allocation table and the image
-// capacity before its copy is issued (*bad on a failed check: nothing more
-// is issued).  A launch that ends without publishing a group
-// has recorded its error in the result, which finish() reports.  On return
-// the library stream is ordered after every copy issued, and after them a
-// stamp marks the end of the copy phase.
+// Copy streams the copy-engine form deals its runs over ($SNAP_DMA_STREAMS,
+// default 1).
 static int dma_streams()
 {
     const char *e = std::getenv("SNAP_DMA_STREAMS");
@@ -1155,11 +1147,23 @@ static int dma_streams()
     return std::max(1, std::min(n, kDmaStreams));
 }
 
-static int dma_dirty_runs(snap_set_s *s, uint8_t *image, uint64_t cap, double deadline, bool *bad)
+// Copy-engine form, host side: while the fused launch runs, take its groups
+// in order as the metadata CTA publishes them and hand each dirty run to
+// the copy engines (one asynchronous copy each, into the caller's pinned
+// image, the runs dealt round-robin over dma_streams() copy streams).
+// Each entry is checked against the allocation table and the image extent
+// `cap` before its copy is issued (*bad on a failed check: nothing more is
+// issued).  A launch that ends without publishing a group sets
+// *unpublished (it has normally recorded its error in the result, which
+// finish() reports).  On return the library stream is ordered after every
+// copy issued, and after them a stamp marks the end of the copy phase.
+static int dma_dirty_runs(snap_set_s *s, uint8_t *image, uint64_t cap, double deadline, bool *bad,
+                          bool *unpublished)
 {
     const FusedIncr &f = s->h_cb->fused;
     const uint64_t nst = (uint64_t)dma_streams();
     *bad = false;
+    *unpublished = false;
     cudaError_t e = cudaEventRecord(s->ev_graph_end, s->st);
     if (e != cudaSuccess) return cuda_status(e);
     int rc = SNAP_OK;
@@ -1175,7 +1179,11 @@ static int dma_dirty_runs(snap_set_s *s, uint8_t *image, uint64_t cap, double de
             }
             if (++spins > 64) std::this_thread::yield();
         }
-        if (rc != SNAP_OK || !p->ready) break;
+        if (rc != SNAP_OK) break;
+        if (!p->ready) {
+            *unpublished = true;
+            break;
+        }
         std::atomic_thread_fence(std::memory_order_acquire);
         const uint64_t b = p->begin, n = p->count;
         if (b > s->runs_cap || n > s->runs_cap - b) {
@@ -1227,12 +1235,15 @@ static int run_checkpoint(snap_set_s *s, GraphEntry *ge, uint8_t *image, uint64_
     s->call_kernels = ge->kernels;
     int rc = cuda_status(cudaGraphLaunch(ge->exec, s->st));
     if (rc) return rc;
-    bool bad = false;
+    bool bad = false, unpublished = false;
     int rc_dma = SNAP_OK;
     // the copies stay inside the pinned range the direct path was chosen for
-    if (s->dma_call) rc_dma = dma_dirty_runs(s, image, image_extent(s, SNAP_INCREMENTAL, cap), deadline, &bad);
+    if (s->dma_call)
+        rc_dma = dma_dirty_runs(s, image, image_extent(s, SNAP_INCREMENTAL, cap), deadline, &bad, &unpublished);
     rc = finish(s, deadline);
-    if (bad) {
+    // a bad run entry, or a launch that ended without publishing every group
+    // and without recording why: the patch is incomplete
+    if (bad || (unpublished && rc == SNAP_OK)) {
         s->device_err |= ERR_BAD_TILE;
         if (rc == SNAP_OK) rc = SNAP_ECUDA;
     }
