@@ -735,7 +735,7 @@ def _pipeline_state(seed):
     return sizes, ts
 
 
-@pytest.mark.parametrize("form", ["fused", "fused16", "dma", "stages"])
+@pytest.mark.parametrize("form", ["fused", "fused16", "dma", "dma2", "stages"])
 @pytest.mark.parametrize("C", [65536, 16384])
 def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monkeypatch, tmp_path):
     """Large enough for several allocation groups: the pipelined patch (image
@@ -747,11 +747,13 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
     the default), also with a 16-warp hash shape taken from the tuning cache
     (the general kernel instantiation, 512-thread CTAs) and with its dirty
     runs handed to the copy engines (SNAP_INCR_COPY_DMA: one copy per run of
-    consecutive dirty chunks of an allocation), and the launch-per-stage one
-    (SNAP_FUSED_OFF)."""
+    consecutive dirty chunks of an allocation; also dealt over two copy
+    streams), and the launch-per-stage one (SNAP_FUSED_OFF)."""
     import math
     if form == "stages":
         monkeypatch.setenv("SNAP_FUSED_OFF", "1")
+    if form == "dma2":
+        monkeypatch.setenv("SNAP_DMA_STREAMS", "2")
     sizes, ts = _pipeline_state(31)
     if form == "fused16":
         cache = tmp_path / "tune.jsonl"
@@ -760,7 +762,7 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         cache.write_text('{"gpu": "%s", "op": 1, "chunk": %d, "class": %d, "warps": 16, "stages": 2, "piece": 64, '
                          '"chains": 1, "tma": 0, "ctas": %d, "gbs": 1.0}\n' % (torch.cuda.get_device_name(), C, cls, sms))
         monkeypatch.setenv("SNAP_TUNE_CACHE", str(cache))
-    a = make_set(ts, C, incr_copy=snap.INCR_COPY_DMA if form == "dma" else snap.INCR_COPY_SM)
+    a = make_set(ts, C, incr_copy=snap.INCR_COPY_DMA if form.startswith("dma") else snap.INCR_COPY_SM)
     b = make_set(ts, C)
     if form == "fused16":
         assert a.tuning(snap.INCREMENTAL)["warps"] == 16
@@ -795,7 +797,7 @@ def test_pipelined_incremental_matches_oracle_and_the_serial_form(C, form, monke
         assert used_a == exp.size and np.array_equal(pa.view(used_a), exp), name
         assert used_b == exp.size and np.array_equal(pb.view(used_b), exp), name
         assert st_a["dirty_chunks"] == st_b["dirty_chunks"] == nd
-        if form == "dma":  # the fused launch, then a stamp after the copies
+        if form.startswith("dma"):  # the fused launch, then a stamp after the copies
             assert st_a["kernel_launches"] == 4
             assert (st_a["dma_copies"] > 0) == (nd > 0) and st_a["dma_copies"] <= nd
             if name == "all":  # one run per allocation with chunks
