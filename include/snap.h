@@ -301,7 +301,8 @@ SNAP_API int snap_verify(const void *host_image, uint64_t bytes, snap_set s, uin
  * are copied into their slots, all hashes replaced, the generation advanced.
  * base.generation must equal patch.parent_generation (EMISMATCH); both are
  * validated completely before the base is modified (EFORMAT leaves it
- * intact). */
+ * intact; so does ENOMEM, when the host cannot hold the per-allocation
+ * tables of a base whose header claims very many allocations). */
 SNAP_API int snap_apply_patch(void *base_image, uint64_t base_bytes, const void *patch, uint64_t patch_bytes);
 
 /* Copy the committed hash table (all chunks, registration order) to host

@@ -10,6 +10,7 @@
 #include "runtime_internal.h"
 
 #include <cstring>
+#include <new>
 #include <vector>
 
 namespace snapk {
@@ -39,8 +40,18 @@ int apply_patch_host(uint8_t *base, uint64_t base_len, const uint8_t *patch, uin
         return SNAP_EMISMATCH;
     if (hp.parent != hb.generation) return SNAP_EMISMATCH;
     const uint64_t C = hb.chunk_bytes;
-    std::vector<FullRec> fr(hb.n_allocs);
-    std::vector<PatchRec> pr(hb.n_allocs);
+    // The allocation count sizes the tables below, so it is bounded first:
+    // every record of a full image takes at least its 32-byte header, and a
+    // header claiming more allocations than the base can hold is malformed.
+    if (hb.n_allocs > (base_len - SNAP_IMG_HEADER_BYTES) / 32) return SNAP_EFORMAT;
+    std::vector<FullRec> fr;
+    std::vector<PatchRec> pr;
+    try {
+        fr.resize(hb.n_allocs);
+        pr.resize(hb.n_allocs);
+    } catch (...) {  // no exception leaves the C ABI
+        return SNAP_ENOMEM;
+    }
 
     // validate the base
     uint64_t off = SNAP_IMG_HEADER_BYTES, total = 0;
