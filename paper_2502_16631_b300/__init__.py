@@ -170,8 +170,12 @@ def _addr(x) -> int:
     if isinstance(x, HostBuffer):
         return x.ptr
     if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("the library reads and writes one contiguous byte range: pass a contiguous array")
         return x.ctypes.data
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("the library reads and writes one contiguous byte range: pass a contiguous tensor")
         return x.data_ptr()
     raise TypeError("cannot take the address of %r" % type(x))
 
@@ -184,6 +188,26 @@ def _nbytes(x) -> int:
     if hasattr(x, "untyped_storage"):
         return x.numel() * x.element_size()
     raise TypeError("cannot size %r" % type(x))
+
+
+def _span(x, n=None, writable=False):
+    """(address, byte count) of a caller's buffer for a call that reads, or
+    with `writable` writes, its first `n` bytes (all of it by default).  A
+    count beyond a sized buffer, or a read-only array the library would
+    write, is refused here, before the library could touch memory outside
+    the buffer; a raw integer address is passed on with its count as given."""
+    if isinstance(x, int):
+        if n is None:
+            raise TypeError("a raw address needs an explicit byte count")
+        return x, n
+    size = _nbytes(x)
+    if n is None:
+        n = size
+    elif n < 0 or n > size:
+        raise ValueError("byte count %d outside the %d-byte buffer" % (n, size))
+    if writable and isinstance(x, np.ndarray) and not x.flags.writeable:
+        raise ValueError("the library writes this buffer: pass a writable array")
+    return _addr(x), n
 
 
 class HostBuffer:
@@ -238,11 +262,10 @@ class Set:
 
     def register(self, t, nbytes: int | None = None) -> int:
         """Register a device tensor (or a raw device address with nbytes)."""
-        if nbytes is None:
-            nbytes = _nbytes(t)
+        addr, nbytes = _span(t, nbytes)
         if not isinstance(t, int):
             self.tensors.append(t)
-        return _check(_lib().snap_register(self.h, _addr(t), nbytes), "snap_register")
+        return _check(_lib().snap_register(self.h, addr, nbytes), "snap_register")
 
     def prepare(self, layout: bool = True, ring: bool = False, shadow: bool = False) -> None:
         """One-time setup now (device tables, pinned ring, async shadow), not in the first call."""
@@ -256,13 +279,13 @@ class Set:
 
     def checkpoint(self, image, mode: int = FULL, cap: int | None = None) -> int:
         used = ctypes.c_uint64()
-        _check(_lib().snap_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+        _check(_lib().snap_checkpoint(self.h, *_span(image, cap, True), mode,
                                       ctypes.byref(used)), "snap_checkpoint")
         return used.value
 
     def checkpoint_status(self, image, mode: int = FULL, cap: int | None = None):
         used = ctypes.c_uint64()
-        rc = _lib().snap_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+        rc = _lib().snap_checkpoint(self.h, *_span(image, cap, True), mode,
                                     ctypes.byref(used))
         return rc, used.value
 
@@ -271,7 +294,7 @@ class Set:
         _check(self.checkpoint_async_status(image, mode, cap), "snap_checkpoint_async")
 
     def checkpoint_async_status(self, image, mode: int = FULL, cap: int | None = None) -> int:
-        return _lib().snap_checkpoint_async(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode)
+        return _lib().snap_checkpoint_async(self.h, *_span(image, cap, True), mode)
 
     def checkpoint_wait(self, timeout_ms: int = 60000) -> int:
         """Finish the pending asynchronous checkpoint; returns the image bytes."""
@@ -290,14 +313,14 @@ class Set:
         (status, image bytes)."""
         used = ctypes.c_uint64()
         cb = _agree_callback(agree)
-        rc = _lib().snap_checkpoint_coordinated(self.h, _addr(image), _nbytes(image) if cap is None else cap, mode,
+        rc = _lib().snap_checkpoint_coordinated(self.h, *_span(image, cap, True), mode,
                                                 ctypes.byref(used), cb, None)
         return rc, used.value
 
     def restore_coordinated(self, image, agree, nbytes: int | None = None) -> int:
         """One rank of a coordinated restore; returns the status."""
         cb = _agree_callback(agree)
-        return _lib().snap_restore_coordinated(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+        return _lib().snap_restore_coordinated(*_span(image, nbytes), self.h,
                                                cb, None)
 
     def restore(self, image, nbytes: int | None = None) -> None:
@@ -328,7 +351,7 @@ class Set:
 
     def restore_async_status(self, image, first=(), nbytes: int | None = None) -> int:
         arr = (ctypes.c_uint32 * max(1, len(first)))(*first)
-        return _lib().snap_restore_async(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+        return _lib().snap_restore_async(*_span(image, nbytes), self.h,
                                          ctypes.cast(arr, ctypes.c_void_p), len(first))
 
     def restore_ready(self, index: int, stream=None) -> None:
@@ -343,11 +366,11 @@ class Set:
         return _lib().snap_restore_wait(self.h, timeout_ms)
 
     def restore_status(self, image, nbytes: int | None = None) -> int:
-        return _lib().snap_restore(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h)
+        return _lib().snap_restore(*_span(image, nbytes), self.h)
 
     def verify(self, image, nbytes: int | None = None) -> int:
         bad = ctypes.c_uint64()
-        _check(_lib().snap_verify(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h,
+        _check(_lib().snap_verify(*_span(image, nbytes), self.h,
                                   ctypes.byref(bad)), "snap_verify")
         return bad.value
 
@@ -364,17 +387,17 @@ class Set:
         return s.as_dict()
 
     def plain_checkpoint(self, image, cap: int | None = None) -> None:
-        _check(_lib().snap_plain_checkpoint(self.h, _addr(image), _nbytes(image) if cap is None else cap),
+        _check(_lib().snap_plain_checkpoint(self.h, *_span(image, cap, True)),
                "snap_plain_checkpoint")
 
     def plain_restore(self, image, nbytes: int | None = None) -> None:
-        _check(_lib().snap_plain_restore(_addr(image), _nbytes(image) if nbytes is None else nbytes, self.h),
+        _check(_lib().snap_plain_restore(*_span(image, nbytes), self.h),
                "snap_plain_restore")
 
     def autotune(self, mode: int = INCREMENTAL, image=None) -> dict:
         t = Tuning()
-        _check(_lib().snap_autotune(self.h, mode, _addr(image) if image is not None else None,
-                                    _nbytes(image) if image is not None else 0, ctypes.byref(t)),
+        _check(_lib().snap_autotune(self.h, mode, *(_span(image, None, True) if image is not None else (None, 0)),
+                                    ctypes.byref(t)),
                "snap_autotune")
         return {k: getattr(t, k) for k, _ in t._fields_}
 
@@ -391,15 +414,15 @@ def apply_patch(base, patch, base_bytes: int | None = None, patch_bytes: int | N
 
 
 def apply_patch_status(base, patch, base_bytes=None, patch_bytes=None) -> int:
-    return _lib().snap_apply_patch(_addr(base), _nbytes(base) if base_bytes is None else base_bytes,
-                                   _addr(patch), _nbytes(patch) if patch_bytes is None else patch_bytes)
+    return _lib().snap_apply_patch(*_span(base, base_bytes, True), *_span(patch, patch_bytes))
 
 
 def hash_chunks(dev_tensor, chunk_bytes: int, out, nbytes: int | None = None, stream=None) -> None:
     """CRC-32C of every chunk of a device buffer into the device array `out`."""
-    n = _nbytes(dev_tensor) if nbytes is None else nbytes
-    _check(_lib().snap_hash_chunks(_addr(dev_tensor), n, chunk_bytes, _addr(out), _stream_handle(stream)),
-           "snap_hash_chunks")
+    addr, n = _span(dev_tensor, nbytes)
+    if not isinstance(out, int) and chunk_bytes > 0 and _nbytes(out) < 4 * ((n + chunk_bytes - 1) // chunk_bytes):
+        raise ValueError("`out` holds fewer than ceil(nbytes / chunk_bytes) 32-bit hashes")
+    _check(_lib().snap_hash_chunks(addr, n, chunk_bytes, _addr(out), _stream_handle(stream)), "snap_hash_chunks")
 
 
 NOALLOC_MAX_BUFFERS = 1024
@@ -530,8 +553,8 @@ class Server:
 
     def submit(self, tenant: Set, kind: int, image, cap: int | None = None) -> int:
         t = ctypes.c_uint64()
-        _check(_lib().snap_server_submit(self.h, tenant.h, kind, _addr(image),
-                                         _nbytes(image) if cap is None else cap, ctypes.byref(t)),
+        _check(_lib().snap_server_submit(self.h, tenant.h, kind, *_span(image, cap, kind != REQ_RESTORE),
+                                         ctypes.byref(t)),
                "snap_server_submit")
         return t.value
 

@@ -144,3 +144,44 @@ def test_apply_patch_refuses_bad_inputs_and_keeps_the_base():
     # and the untouched inputs still merge
     merged = base.copy()
     assert snap.apply_patch_status(merged, patch) == snap.OK
+
+
+def test_binding_refuses_buffers_the_library_would_overrun():
+    """The binding passes one (address, byte count) range per buffer, so it
+    refuses a view that is not one contiguous range, a count beyond the
+    buffer and, for a buffer the library writes, a read-only array -- before
+    any library call."""
+    C = 4096
+    _, _, base, patch, _ = images(SIZES, C, seed=5)
+    for bad_base in (base[::-1], np.lib.stride_tricks.as_strided(base, (base.size // 2,), (2,))):
+        with pytest.raises(ValueError):
+            snap.apply_patch(bad_base, patch)
+    frozen = base.copy()
+    frozen.flags.writeable = False
+    with pytest.raises(ValueError):
+        snap.apply_patch(frozen, patch)
+    with pytest.raises(ValueError):
+        snap.apply_patch(base.copy(), patch, base_bytes=base.size + 1)
+    with pytest.raises(ValueError):
+        snap.apply_patch(base.copy(), patch, patch_bytes=patch.size + 4096)
+    ro_patch = patch.copy()
+    ro_patch.flags.writeable = False  # a patch is only read
+    merged = base.copy()
+    snap.apply_patch(merged, ro_patch)
+    assert np.array_equal(merged, oracle.write_full(images(SIZES, C, seed=5)[1], C, generation=5)[1])
+
+
+def test_span_of_tensors_and_raw_addresses():
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(64, 64, dtype=torch.uint8)
+    assert snap._span(t) == (t.data_ptr(), 4096)
+    assert snap._span(t[8:16]) == (t[8:16].data_ptr(), 512)
+    with pytest.raises(ValueError):
+        snap._span(t.t())
+    with pytest.raises(ValueError):
+        snap._span(t[:, :8])
+    with pytest.raises(ValueError):
+        snap._span(t, 4097)
+    assert snap._span(12345, 7) == (12345, 7)
+    with pytest.raises(TypeError):
+        snap._span(12345)
